@@ -1,0 +1,200 @@
+"""CPU oracle for the incoherent harmonic sum (arXiv:1812.02647, Eq. 1-4) -- TEST INFRASTRUCTURE.
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's ``cpu_baseline`` / reference legs
+may import this package.  It is plain C (``hs_oracle.c``) behind ctypes, built with gcc
+``-O2 -ffp-contract=off`` (no FMA contraction, no fast-math) so that its FP32 mode rounds every
+operation in the order the definitions are written.  It shares no code with the GPU library.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py`` against closed
+forms, brute force, special cases and hand-worked fixtures (``tests/golden``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+STD, MAX, FBIN, GREEDY = 1, 2, 4, 8
+VARIANTS = {"std": STD, "max": MAX, "fbin": FBIN, "greedy": GREEDY}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRCS = [os.path.join(_HERE, "hs_oracle.c"), os.path.join(_HERE, "hs_oracle_body.h")]
+_LIB = os.path.join(_HERE, "libhs_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle in place with gcc (OpenMP when available)."""
+    newest = max(os.path.getmtime(s) for s in _SRCS)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+    tmp = _LIB + ".tmp%d" % os.getpid()
+    try:
+        subprocess.run(base + ["-fopenmp", _SRCS[0], "-o", tmp, "-lm"], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + [_SRCS[0], "-o", tmp, "-lm"], check=True, capture_output=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        P, I, I64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        lib.hs_oracle_hvalid.argtypes = [I, I64, I64, I]
+        lib.hs_oracle_hvalid.restype = I
+        for sfx in ("f32", "f64"):
+            getattr(lib, "hs_oracle_1d_" + sfx).argtypes = [I, P, I64, I, P, P, P, P, P, P, I]
+            getattr(lib, "hs_oracle_batched_" + sfx).argtypes = [I, P, P, I, I, P, P, P, P, P, I]
+            getattr(lib, "hs_oracle_2d_" + sfx).argtypes = [P, I, I, I64, I64, I, P, P, P, P, P, P, P, P, I]
+        lib.hs_oracle_grad_f64.argtypes = [I, P, I64, I, P, P, P, P]
+        lib.hs_oracle_standardize_cast.argtypes = [P, I64, ctypes.c_float, ctypes.c_float, I, P]
+        lib.hs_oracle_noise_moments.argtypes = [I, I, P, P]
+        lib.hs_oracle_max_threads.restype = I
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _variant(v):
+    return VARIANTS[v] if isinstance(v, str) else int(v)
+
+
+def _threads(n):
+    return int(n) if n else 1
+
+
+def max_threads() -> int:
+    return _load().hs_oracle_max_threads()
+
+
+def hvalid(variant, n: int, N: int, hmax: int) -> int:
+    return _load().hs_oracle_hvalid(_variant(variant), n, N, hmax)
+
+
+def _tables(mu, isig, hmax, dt):
+    mu = None if mu is None else np.ascontiguousarray(mu, dtype=dt)
+    isig = None if isig is None else np.ascontiguousarray(isig, dtype=dt)
+    for t in (mu, isig):
+        if t is not None and t.shape[0] < hmax + 1:
+            raise ValueError("calibration tables need hmax+1 entries")
+    return mu, isig
+
+
+def hs_1d(variant, x, hmax: int = 32, mu=None, isig=None, fp64: bool = False, all_h: bool = False,
+          nthreads: int | None = None):
+    """Per-bin best snr / H (and the greedy path, and optionally every H's snr) of one spectrum.
+
+    FP32 mode takes float32 input; FP64 mode widens the input to float64 and computes in double.
+    """
+    v = _variant(variant)
+    dt = np.float64 if fp64 else np.float32
+    x = np.ascontiguousarray(x, dtype=dt)
+    N = x.shape[0]
+    mu, isig = _tables(mu, isig, hmax, dt)
+    best = np.empty(N, dt)
+    bh = np.empty(N, np.uint8)
+    path = np.zeros(N, np.uint32) if v == GREEDY else None
+    ah = np.empty((hmax, N), dt) if all_h else None
+    fn = _load().hs_oracle_1d_f64 if fp64 else _load().hs_oracle_1d_f32
+    fn(v, _ptr(x), N, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh), _ptr(path), _ptr(ah), _threads(nthreads))
+    out = {"best_snr": best, "best_h": bh}
+    if path is not None:
+        out["path"] = path
+    if ah is not None:
+        out["all_h"] = ah
+    return out
+
+
+def hs_batched(variant, x, offsets, hmax: int = 32, mu=None, isig=None, fp64: bool = False,
+               nthreads: int | None = None):
+    v = _variant(variant)
+    dt = np.float64 if fp64 else np.float32
+    x = np.ascontiguousarray(x, dtype=dt)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    base = int(offsets[0])
+    offs = offsets - base
+    total = int(offs[-1])
+    mu, isig = _tables(mu, isig, hmax, dt)
+    best = np.empty(total, dt)
+    bh = np.empty(total, np.uint8)
+    path = np.zeros(total, np.uint32) if v == GREEDY else None
+    fn = _load().hs_oracle_batched_f64 if fp64 else _load().hs_oracle_batched_f32
+    fn(v, _ptr(x[base:base + total]), _ptr(offs), len(offs) - 1, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh),
+       _ptr(path), _threads(nthreads))
+    out = {"best_snr": best, "best_h": bh}
+    if path is not None:
+        out["path"] = path
+    return out
+
+
+def hs_2d(plane, z_min: int, hmax: int = 16, mu=None, isig=None, fp64: bool = False, all_h: bool = False,
+          nthreads: int | None = None):
+    """2-D Eq. 1 over a (nz, n_bins) plane whose row r holds z = z_min + r."""
+    dt = np.float64 if fp64 else np.float32
+    plane = np.ascontiguousarray(plane, dtype=dt)
+    nz, nb = plane.shape
+    mu, isig = _tables(mu, isig, hmax, dt)
+    best = np.empty((nz, nb), dt)
+    bh = np.empty((nz, nb), np.uint8)
+    bn = np.empty(nb, dt)
+    bhn = np.empty(nb, np.uint8)
+    bzn = np.empty(nb, np.int32)
+    ah = np.empty((hmax, nz, nb), dt) if all_h else None
+    fn = _load().hs_oracle_2d_f64 if fp64 else _load().hs_oracle_2d_f32
+    fn(_ptr(plane), nz, z_min, nb, nb, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh), _ptr(bn), _ptr(bhn),
+       _ptr(bzn), _ptr(ah), _threads(nthreads))
+    out = {"best_snr": best, "best_h": bh, "best_snr_n": bn, "best_h_n": bhn, "best_z_n": bzn}
+    if ah is not None:
+        out["all_h"] = ah
+    return out
+
+
+def grad_1d(variant, x, g, best_h, hmax: int = 32, isig=None):
+    """FP64 adjoint: d/dx of sum_n g[n] * best_snr[n] with the best H of each bin held fixed."""
+    v = _variant(variant)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    best_h = np.ascontiguousarray(best_h, dtype=np.uint8)
+    isig = None if isig is None else np.ascontiguousarray(isig, dtype=np.float64)
+    out = np.zeros_like(x)
+    _load().hs_oracle_grad_f64(v, _ptr(x), x.shape[0], hmax, _ptr(isig), _ptr(g), _ptr(best_h), _ptr(out))
+    return out
+
+
+def standardize_cast(p, mu: float, sigma: float, dtype: str):
+    """(p - mu) / sigma in FP32, rounded to nearest-even FP16 or BF16; returns the uint16 bit patterns."""
+    p = np.ascontiguousarray(p, dtype=np.float32)
+    out = np.empty(p.shape, np.uint16)
+    code = {"f16": 1, "bf16": 2}[dtype]
+    _load().hs_oracle_standardize_cast(_ptr(p), p.size, float(mu), float(sigma), code, _ptr(out))
+    return out
+
+
+def noise_moments(variant, hmax: int = 32):
+    """Closed-form (mu_H, sigma_H) of h_H on standardised Exp(1) noise, H = 0..hmax (double)."""
+    mu = np.empty(hmax + 1, np.float64)
+    sd = np.empty(hmax + 1, np.float64)
+    _load().hs_oracle_noise_moments(_variant(variant), hmax, _ptr(mu), _ptr(sd))
+    return mu, sd
+
+
+def noise_calibration(variant, hmax: int = 32):
+    """The float32 (mu_H, 1/sigma_H) tables derived from ``noise_moments``, rounded once."""
+    mu, sd = noise_moments(variant, hmax)
+    return mu.astype(np.float32), (1.0 / sd).astype(np.float32)
+
+
+def candidates(best_snr, best_h, threshold: float, spectrum: int = 0):
+    """The thresholded candidate set: every bin whose best snr is strictly above the threshold,
+    as (spectrum, bin, snr, H) rows in bin order."""
+    idx = np.nonzero(best_snr > threshold)[0]
+    return np.stack([np.full(idx.shape, spectrum, np.int64), idx.astype(np.int64)], 1), best_snr[idx], best_h[idx]
