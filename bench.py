@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 harmonic-sum library on the batched DM-trial workload.
+
+Workload (one step): 2048 synthetic DM-trial spectra, lengths drawn uniformly from {2^19, 2^20,
+2^21, 2^22} bins (4.02 G bins, 16.1 GB FP32), standardised exponential noise with pulsars injected
+in 5% of them; all four harmonic-sum variants (Eq. 1-4), H = 1..32, per-bin best snr / H, the
+Eq. 4 path, and candidates above 6.  Each variant is one persistent launch over a (spectrum, tile)
+work queue, replayed from a CUDA graph.  The input is resident in HBM when the timed region starts
+(it is larger than L2, so no flush is needed).
+
+metric: harmonic-summed bins/s = (input bins x H_max) / step time, a step running all four
+variants; under torchrun every rank processes its own batch (weak scaling) and the value counts
+all ranks' bins over the slowest rank's time.
+
+``--impl reference`` times the CPU oracle (the reference arm of this project: a plain C evaluation
+of the paper's equations) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import hs_synth  # noqa: E402
+
+METRIC = "harmonic-summed bins/sec (input bins x H_max)"
+UNIT = "bins*H/s"
+HMAX = 32
+VARIANTS = ("std", "max", "fbin", "greedy")
+THR = 6.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--spectra", type=int, default=2048, help="spectra in the batch (2048 is the workload)")
+    ap.add_argument("--variants", default=",".join(VARIANTS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--cpu-sample-spectra", type=int, default=16)
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]",) else 0.0,
+                             parts[5], parts[6], parts[7], parts[8]))
+            except ValueError:
+                continue
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [r[0] for r in rows]
+        reasons = set()
+        for r in rows:
+            for name, val in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"), r[3:]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_setup():
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def reduce_max(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(offsets, x_host, n_sample, variants, cores, reps=1):
+    """Time the oracle's FP32 mode on the first n_sample spectra of the batch (all host cores,
+    one spectrum per thread as in the paper's CPU versions)."""
+    import oracle
+
+    offs = offsets[: n_sample + 1].copy()
+    xs = np.asarray(x_host[: int(offs[-1])])
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        for v in variants:
+            mu, isig = oracle.noise_calibration(v, HMAX)
+            oracle.hs_batched(v, xs, offs, hmax=HMAX, mu=mu, isig=isig, nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    bins = int(offs[-1])
+    return bins, statistics.median(times)
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle on a bounded sample, rank 0 only."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    variants = tuple(args.variants.split(","))
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(args.spectra)
+    n_sample = 4
+    x = hs_synth.batch(seed, offsets[: n_sample + 1], pulsars[:n_sample])
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        cpu_oracle_sample(offsets, x, n_sample, variants, cores)
+    times = []
+    for _ in range(args.steps):
+        bins, t = cpu_oracle_sample(offsets, x, n_sample, variants, cores)
+        times.append(t)
+    step = statistics.mean(times)
+    value = bins * HMAX / step
+    sample = "%d of %d spectra (%d bins), %s" % (n_sample, args.spectra, bins, "+".join(variants))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(args, offsets, variants),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def workload_config(args, offsets, variants):
+    return {"workload": "batched DM-trial spectra: %d spectra, lengths uniform in {2^19..2^22} bins, FP32, "
+                        "H_max=32, variants %s, persistent graph-captured launch per variant" %
+                        (args.spectra, "+".join(variants)),
+            "n_spectra": args.spectra, "total_bins": int(offsets[-1]), "hmax": HMAX, "variants": list(variants),
+            "threshold": THR, "l2": "inputs (%.1f GB) larger than L2; no flush" % (offsets[-1] * 4 / 1e9)}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_1812_02647_gb300 as hs
+
+    rank, world, local = dist_setup()
+    variants = tuple(args.variants.split(","))
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(args.spectra, trial=rank)
+    total = int(offsets[-1])
+    x_host = torch.empty(total, dtype=torch.float32, pin_memory=True)
+    hs_synth.batch(seed, offsets, pulsars, out=x_host.data_ptr())
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        xd = torch.empty(total, dtype=torch.float32, device="cuda")
+        xd.copy_(x_host, non_blocking=True)
+        od = torch.from_numpy(offsets).cuda()
+        cap = 1 << 24
+        h = hs.HarmonicSum(variants=0xF, hmax=HMAX, max_bins=1 << 22, threshold=THR, cand_capacity=cap,
+                           max_spectra=args.spectra)
+        for v in variants:
+            mu, isig = hs.hs_noise_calibration(v, HMAX)
+            h.set_calibration(v, mu, isig)
+        if args.autotune:
+            n_t = 1 << 22
+            scratch = torch.empty(n_t * 4 + n_t * 9 + 4096, dtype=torch.uint8, device="cuda")
+            scratch[: n_t * 4].view(torch.float32).copy_(xd[:n_t])
+            for v in variants:
+                hs.hs_autotune(h.plan, v, n_t, scratch, h.ws)
+            del scratch
+        outs = {v: h.new_outputs(total, v, "cuda") for v in variants}
+        graphs = {v: hs.hs_graph_create_batched(h.plan, hs.VARIANTS[v], xd, od, [h.out_struct(outs[v])], h.ws)
+                  for v in variants}
+        ev = {v: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for v in variants}
+        per_variant = {v: [] for v in variants}
+
+        def step(record=False):
+            for v in variants:
+                outs[v]["cand_count"].zero_()
+                if record:
+                    ev[v][0].record(stream)
+                hs.hs_graph_launch(graphs[v], stream)
+                if record:
+                    ev[v][1].record(stream)
+            if record:
+                stream.synchronize()
+                for v in variants:
+                    per_variant[v].append(ev[v][0].elapsed_time(ev[v][1]))
+
+        for _ in range(max(args.warmup, 0)):
+            step()
+        torch.cuda.synchronize()
+        assert h.sync_status(stream) in (hs.OK, hs.WARN_CAND_OVERFLOW)
+
+        # per-variant launch durations, measured on the launching stream (separate pass, same work)
+        for _ in range(max(2, min(args.steps, 5))):
+            step(record=True)
+
+        clocks = ClockSampler(local)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(world)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        clk = clocks.stop()
+        step_ms = reduce_max(e0.elapsed_time(e1) / args.steps, world)
+        n_cands = {v: int(outs[v]["cand_count"].item()) for v in variants}
+
+        # end to end through the public API: pinned host input -> device, all variants, candidates back
+        e2e = None
+        if not args.no_e2e:
+            cand_host = {v: torch.empty(cap * 16, dtype=torch.uint8, pin_memory=True) for v in variants}
+            cnt_host = torch.empty(len(variants), dtype=torch.int64, pin_memory=True)
+            k_e2e = max(1, min(args.steps, 3))
+            d2h = 0
+            barrier(world)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(k_e2e):
+                xd.copy_(x_host, non_blocking=True)
+                step()
+                for i, v in enumerate(variants):
+                    cnt_host[i : i + 1].copy_(outs[v]["cand_count"], non_blocking=True)
+                stream.synchronize()
+                d2h += 8 * len(variants)
+                for i, v in enumerate(variants):
+                    n = min(int(cnt_host[i]), cap)
+                    cand_host[v][: n * 16].copy_(outs[v]["cand"][: n * 16], non_blocking=True)
+                    d2h += n * 16
+                stream.synchronize()
+            t_e2e = reduce_max((time.perf_counter() - t0) / k_e2e, world)
+            e2e = {"value": world * total * HMAX / t_e2e, "unit": UNIT, "h2d_bytes_per_step": total * 4,
+                   "d2h_bytes_per_step": d2h // k_e2e, "ms_per_step": t_e2e * 1e3}
+
+    value = world * total * HMAX / (step_ms / 1e3)
+    peaks, peak_src = load_peaks()
+    avg = {v: statistics.mean(per_variant[v]) for v in variants}
+    dom = max(avg, key=avg.get)
+    out_bytes = 4 + 1 + (4 if dom == "greedy" else 0)
+    alg_bytes = total * (4 + out_bytes)
+    achieved = alg_bytes / (avg[dom] / 1e3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": workload_config(args, offsets, variants),
+        "gpu_launches": args.steps * 2 * len(variants),
+        "per_variant_ms": avg,
+        "per_variant_compulsory_gbs": {v: total * (8 + 1 + (4 if v == "greedy" else 0)) / (avg[v] / 1e3) / 1e9
+                                       for v in variants},
+        "candidates": n_cands,
+        "roofline": {"bound": "hbm", "kernel": "hs1d persistent, %s" % dom, "achieved": achieved,
+                     "peak": peaks["hbm_gbs"], "peak_source": peak_src, "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "algorithmic_bytes_per_launch": alg_bytes},
+        "clocks": clk,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        n_s = min(args.cpu_sample_spectra, args.spectra)
+        bins, t = cpu_oracle_sample(offsets, x_host.numpy(), n_s, variants, cores)
+        line["cpu_baseline"] = {"value": bins * HMAX / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": "first %d spectra (%d bins), all listed variants, FP32 oracle" % (n_s, bins)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

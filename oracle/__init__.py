@@ -50,6 +50,8 @@ def _load():
         lib.hs_oracle_hvalid.restype = I
         for sfx in ("f32", "f64"):
             getattr(lib, "hs_oracle_1d_" + sfx).argtypes = [I, P, I64, I, P, P, P, P, P, P, I]
+            getattr(lib, "hs_oracle_bins_" + sfx).argtypes = [I, P, I64, I, P, P, P, I64, P, P, P]
+            getattr(lib, "hs_oracle_2d_cells_" + sfx).argtypes = [P, I, I, I64, I64, I, P, P, P, P, I64, P, P]
             getattr(lib, "hs_oracle_batched_" + sfx).argtypes = [I, P, P, I, I, P, P, P, P, P, I]
             getattr(lib, "hs_oracle_2d_" + sfx).argtypes = [P, I, I, I64, I64, I, P, P, P, P, P, P, P, P, I]
         lib.hs_oracle_grad_f64.argtypes = [I, P, I64, I, P, P, P, P]
@@ -114,6 +116,23 @@ def hs_1d(variant, x, hmax: int = 32, mu=None, isig=None, fp64: bool = False, al
     return out
 
 
+def hs_bins(variant, x, bins, hmax: int = 32, mu=None, isig=None, fp64: bool = False):
+    """Best snr / H / path of the listed output bins of one spectrum only."""
+    v = _variant(variant)
+    dt = np.float64 if fp64 else np.float32
+    x = np.ascontiguousarray(x, dtype=dt)
+    bins = np.ascontiguousarray(bins, dtype=np.int64)
+    if bins.size and (bins.min() < 0 or bins.max() >= x.shape[0]):
+        raise ValueError("bin out of range")
+    mu, isig = _tables(mu, isig, hmax, dt)
+    best = np.empty(bins.size, dt)
+    bh = np.empty(bins.size, np.uint8)
+    path = np.zeros(bins.size, np.uint32)
+    fn = _load().hs_oracle_bins_f64 if fp64 else _load().hs_oracle_bins_f32
+    fn(v, _ptr(x), x.shape[0], hmax, _ptr(mu), _ptr(isig), _ptr(bins), bins.size, _ptr(best), _ptr(bh), _ptr(path))
+    return {"best_snr": best, "best_h": bh, "path": path}
+
+
 def hs_batched(variant, x, offsets, hmax: int = 32, mu=None, isig=None, fp64: bool = False,
                nthreads: int | None = None):
     v = _variant(variant)
@@ -156,6 +175,24 @@ def hs_2d(plane, z_min: int, hmax: int = 16, mu=None, isig=None, fp64: bool = Fa
     if ah is not None:
         out["all_h"] = ah
     return out
+
+
+def hs_2d_cells(plane, z_min: int, rows, bins, hmax: int = 16, mu=None, isig=None, fp64: bool = False):
+    """Best snr / H of the listed (row, bin) cells of a 2-D plane only."""
+    dt = np.float64 if fp64 else np.float32
+    plane = np.ascontiguousarray(plane, dtype=dt)
+    nz, nb = plane.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    bins = np.ascontiguousarray(bins, dtype=np.int64)
+    if rows.size and (rows.min() < 0 or rows.max() >= nz or bins.min() < 0 or bins.max() >= nb):
+        raise ValueError("cell out of range")
+    mu, isig = _tables(mu, isig, hmax, dt)
+    best = np.empty(rows.size, dt)
+    bh = np.empty(rows.size, np.uint8)
+    fn = _load().hs_oracle_2d_cells_f64 if fp64 else _load().hs_oracle_2d_cells_f32
+    fn(_ptr(plane), nz, z_min, nb, nb, hmax, _ptr(mu), _ptr(isig), _ptr(rows), _ptr(bins), rows.size, _ptr(best),
+       _ptr(bh))
+    return {"best_snr": best, "best_h": bh}
 
 
 def grad_1d(variant, x, g, best_h, hmax: int = 32, isig=None):

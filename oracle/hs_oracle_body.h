@@ -69,9 +69,9 @@ static void FN(hs_bin_)(int variant, const REAL* x, int64_t N, int64_t n, int hm
         }
         if (all_h) all_h[(int64_t)(H - 1) * all_h_stride + n] = snr;
     }
-    best_out[n] = best;
-    h_out[n] = (uint8_t)best_h;
-    if (path_out) path_out[n] = path;
+    *best_out = best;
+    *h_out = (uint8_t)best_h;
+    if (path_out) *path_out = path;
 }
 
 /* One spectrum, every bin; bins are independent, so they may run on several threads. */
@@ -86,7 +86,23 @@ void FN(hs_oracle_1d_)(int variant, const REAL* x, int64_t N, int hmax, const RE
     }
 #pragma omp parallel for schedule(dynamic, 2048) num_threads(nthreads > 0 ? nthreads : 1) if (nthreads > 1)
     for (int64_t n = 0; n < N; ++n)
-        FN(hs_bin_)(variant, x, N, n, hmax, cs, mu, isig, best_snr, best_h, path, all_h, N);
+        FN(hs_bin_)(variant, x, N, n, hmax, cs, mu, isig, &best_snr[n], &best_h[n], path ? &path[n] : NULL, all_h, N);
+}
+
+/* Only the listed output bins of one spectrum (for spot checks of very large inputs). */
+void FN(hs_oracle_bins_)(int variant, const REAL* x, int64_t N, int hmax, const REAL* mu_in, const REAL* isig_in,
+                         const int64_t* bins, int64_t count, REAL* best_snr, uint8_t* best_h, uint32_t* path) {
+    REAL cs[HS_O_HMAX + 1], mu[HS_O_HMAX + 1], isig[HS_O_HMAX + 1];
+    for (int H = 0; H <= hmax; ++H) {
+        cs[H] = (H == 0) ? (REAL)0 : (REAL)(1.0 / sqrt((double)H));
+        mu[H] = mu_in ? mu_in[H] : (REAL)0;
+        isig[H] = isig_in ? isig_in[H] : (REAL)1;
+    }
+    for (int64_t k = 0; k < count; ++k) {
+        uint32_t pth = 0;
+        FN(hs_bin_)(variant, x, N, bins[k], hmax, cs, mu, isig, &best_snr[k], &best_h[k], &pth, NULL, N);
+        if (path) path[k] = pth;
+    }
 }
 
 /* A packed batch: spectrum s is x[offsets[s] .. offsets[s+1]); outputs use the same packing.
@@ -154,6 +170,39 @@ void FN(hs_oracle_2d_)(const REAL* plane, int nz, int z_min, int64_t n_bins, int
         best_snr_n[n] = best;
         best_h_n[n] = best_h[(int64_t)br * n_bins + n];
         best_z_n[n] = z_min + br;
+    }
+}
+
+/* Only the listed cells (row rows[k], bin bins[k]) of a 2-D plane, same definition as above. */
+void FN(hs_oracle_2d_cells_)(const REAL* plane, int nz, int z_min, int64_t n_bins, int64_t row_stride, int hmax,
+                             const REAL* mu_in, const REAL* isig_in, const int32_t* rows, const int64_t* bins,
+                             int64_t count, REAL* best_snr, uint8_t* best_h) {
+    REAL cs[HS_O_HMAX + 1], mu[HS_O_HMAX + 1], isig[HS_O_HMAX + 1];
+    for (int H = 0; H <= hmax; ++H) {
+        cs[H] = (H == 0) ? (REAL)0 : (REAL)(1.0 / sqrt((double)H));
+        mu[H] = mu_in ? mu_in[H] : (REAL)0;
+        isig[H] = isig_in ? isig_in[H] : (REAL)1;
+    }
+    (void)nz;
+    (void)n_bins;
+    for (int64_t k = 0; k < count; ++k) {
+        int64_t z = (int64_t)z_min + rows[k], n = bins[k];
+        REAL best = -INFINITY;
+        int bh = 0;
+        for (int H = 1; H <= hmax; ++H) {
+            REAL sum = 0;
+            for (int i = 1; i <= H; ++i) {
+                int64_t zi = hs_oracle_floor_div(2 * z * i + H, 2 * (int64_t)H);
+                sum = sum + plane[(zi - z_min) * row_stride + hs_oracle_eq1_index(n, i, H)];
+            }
+            REAL snr = (sum * cs[H] - mu[H]) * isig[H];
+            if (snr > best) {
+                best = snr;
+                bh = H;
+            }
+        }
+        best_snr[k] = best;
+        best_h[k] = (uint8_t)bh;
     }
 }
 

@@ -1,0 +1,242 @@
+// Auxiliary device steps: standardise + cast to FP16/BF16 storage, and a stable LSD radix sort of
+// the candidate list by (variant, spectrum, z, bin).
+#include <algorithm>
+
+#include "hs_common.cuh"
+
+namespace hs {
+
+// ------------------------------------------------------------------------------------------
+// y = (p - mu_s) / sigma_s in FP32 (IEEE division), rounded to nearest even FP16 / BF16.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T narrow(float y);
+template <>
+__device__ __forceinline__ __half narrow<__half>(float y) {
+    return __float2half_rn(y);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 narrow<__nv_bfloat16>(float y) {
+    return __float2bfloat16_rn(y);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_standardize_cast(const float* p, const int64_t* offsets, int64_t n_bins,
+                                                          const float* mu, const float* sigma, T* out) {
+    const int s = blockIdx.y;
+    const int64_t off = offsets ? offsets[s] : 0;
+    const int64_t N = offsets ? offsets[s + 1] - off : n_bins;
+    const float m = mu[s], sd = sigma[s];
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
+        out[off + k] = narrow<T>(__fdiv_rn(__fsub_rn(p[off + k], m), sd));
+}
+
+cudaError_t launch_standardize_cast(const float* p, const int64_t* offsets, int n_spectra, int64_t n_bins,
+                                    const float* mu, const float* sigma, hs_dtype dt, void* out, cudaStream_t s) {
+    unsigned gx = (unsigned)std::min<int64_t>((n_bins + 255) / 256, 4096);
+    if (gx == 0 || n_spectra == 0) return cudaSuccess;
+    dim3 grid(gx, (unsigned)n_spectra);
+    if (dt == HS_F16)
+        k_standardize_cast<__half><<<grid, 256, 0, s>>>(p, offsets, n_bins, mu, sigma, (__half*)out);
+    else
+        k_standardize_cast<__nv_bfloat16><<<grid, 256, 0, s>>>(p, offsets, n_bins, mu, sigma, (__nv_bfloat16*)out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------
+// Candidate sort.  Key digits, least significant first: bin (4 bytes), z (2 bytes, offset by
+// 2^15), spectrum (4 bytes), variant (1 byte).  A digit that is the same for every candidate is
+// copied through instead of scattered.  The count is read on the device, so the launch shapes
+// cover the capacity and blocks beyond the count exit.
+// ------------------------------------------------------------------------------------------
+constexpr int kSortBlock = 256;
+constexpr int kSortPer = 16;
+constexpr int kSortChunk = kSortBlock * kSortPer;
+constexpr int kSortPasses = 11;
+
+__device__ __forceinline__ unsigned cand_digit(const uint4& c, int pass) {
+    switch (pass) {
+        case 0: case 1: case 2: case 3: return (c.y >> (8 * pass)) & 0xffu;             // bin
+        case 4: case 5: return (((c.w & 0xffffu) ^ 0x8000u) >> (8 * (pass - 4))) & 0xffu;  // z, biased
+        case 6: case 7: case 8: case 9: return (c.x >> (8 * (pass - 6))) & 0xffu;        // spectrum
+        default: return (c.w >> 24) & 0xffu;                                              // variant
+    }
+}
+
+struct SortCtl {
+    unsigned long long n;     // number of candidates to sort
+    unsigned dig_or[kSortPasses];
+    unsigned dig_and[kSortPasses];
+};
+
+__global__ void k_sort_init(const unsigned long long* count, long long cap, SortCtl* sc) {
+    if (threadIdx.x == 0) {
+        unsigned long long c = *count;
+        sc->n = c < (unsigned long long)cap ? c : (unsigned long long)cap;
+    }
+    if (threadIdx.x < kSortPasses) {
+        sc->dig_or[threadIdx.x] = 0u;
+        sc->dig_and[threadIdx.x] = 0xffu;
+    }
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_sort_digits(const uint4* c, SortCtl* sc) {
+    const unsigned long long n = sc->n;
+    unsigned o[kSortPasses], a[kSortPasses];
+    for (int p = 0; p < kSortPasses; ++p) {
+        o[p] = 0u;
+        a[p] = 0xffu;
+    }
+    for (unsigned long long k = (unsigned long long)blockIdx.x * kSortBlock + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * kSortBlock) {
+        uint4 v = c[k];
+        for (int p = 0; p < kSortPasses; ++p) {
+            unsigned d = cand_digit(v, p);
+            o[p] |= d;
+            a[p] &= d;
+        }
+    }
+    for (int p = 0; p < kSortPasses; ++p) {
+        atomicOr(&sc->dig_or[p], o[p]);
+        atomicAnd(&sc->dig_and[p], a[p]);
+    }
+}
+
+__device__ __forceinline__ bool pass_skipped(const SortCtl* sc, int pass) {
+    return (sc->dig_or[pass] ^ sc->dig_and[pass]) == 0u;
+}
+
+// per-block digit histograms, stored digit-major: hist[d * nblocks + block]
+__global__ void __launch_bounds__(kSortBlock) k_sort_hist(const uint4* src, const SortCtl* sc, int pass,
+                                                          unsigned* hist, int nblocks) {
+    __shared__ unsigned h[256];
+    if (pass_skipped(sc, pass)) return;
+    const unsigned long long n = sc->n;
+    h[threadIdx.x] = 0u;
+    __syncthreads();
+    const unsigned long long c0 = (unsigned long long)blockIdx.x * kSortChunk;
+    for (int k = threadIdx.x; k < kSortChunk; k += kSortBlock) {
+        unsigned long long i = c0 + k;
+        if (i < n) atomicAdd(&h[cand_digit(src[i], pass)], 1u);
+    }
+    __syncthreads();
+    hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of hist (256 * nblocks entries) in place, one block
+__global__ void __launch_bounds__(1024) k_sort_scan(const SortCtl* sc, int pass, unsigned* hist, int total) {
+    __shared__ unsigned ws[32];
+    __shared__ unsigned carry;
+    if (pass_skipped(sc, pass)) return;
+    if (threadIdx.x == 0) carry = 0u;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int base = 0; base < total; base += 1024) {
+        int i = base + threadIdx.x;
+        unsigned t = i < total ? hist[i] : 0u, v = t;
+        for (int d = 1; d < 32; d <<= 1) {
+            unsigned u = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) v += u;
+        }
+        if (lane == 31) ws[wid] = v;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned x = ws[lane];
+            for (int d = 1; d < 32; d <<= 1) {
+                unsigned u = __shfl_up_sync(0xffffffffu, x, d);
+                if (lane >= d) x += u;
+            }
+            ws[lane] = x;
+        }
+        __syncthreads();
+        unsigned excl = carry + (wid ? ws[wid - 1] : 0u) + v - t;
+        if (i < total) hist[i] = excl;
+        __syncthreads();
+        if (threadIdx.x == 1023) carry = excl + t;
+        __syncthreads();
+    }
+}
+
+// stable scatter: warp w of a block owns the w-th contiguous slice of the block's chunk
+__global__ void __launch_bounds__(kSortBlock) k_sort_scatter(const uint4* src, uint4* dst, const SortCtl* sc,
+                                                             int pass, const unsigned* hist, int nblocks) {
+    constexpr int kWarps = kSortBlock / 32;
+    constexpr int kSlice = kSortChunk / kWarps;
+    __shared__ unsigned wbase[kWarps][256];
+    const unsigned long long n = sc->n;
+    const unsigned long long c0 = (unsigned long long)blockIdx.x * kSortChunk;
+    if (c0 >= n) return;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (pass_skipped(sc, pass)) {
+        for (int k = threadIdx.x; k < kSortChunk; k += kSortBlock) {
+            unsigned long long i = c0 + k;
+            if (i < n) dst[i] = src[i];
+        }
+        return;
+    }
+    for (int d = lane; d < 256; d += 32) wbase[w][d] = 0u;
+    __syncwarp();
+    const unsigned long long s0 = c0 + (unsigned long long)w * kSlice;
+    for (int k = 0; k < kSlice; k += 32) {  // count this warp's digits
+        unsigned long long i = s0 + k + lane;
+        if (i < n) atomicAdd(&wbase[w][cand_digit(src[i], pass)], 1u);
+    }
+    __syncthreads();
+    // per digit: exclusive prefix over warps, plus the block's global base
+    for (int d = threadIdx.x; d < 256; d += kSortBlock) {
+        unsigned run = hist[(size_t)d * nblocks + blockIdx.x];
+        for (int k = 0; k < kWarps; ++k) {
+            unsigned c = wbase[k][d];
+            wbase[k][d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < kSlice; k += 32) {
+        unsigned long long i = s0 + k + lane;
+        bool ok = i < n;
+        uint4 v = ok ? src[i] : make_uint4(0, 0, 0, 0);
+        unsigned d = ok ? cand_digit(v, pass) : 0xffffffffu;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        unsigned rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok) dst[wbase[w][d] + rank] = v;
+        __syncwarp();
+        if (ok && rank == 0) wbase[w][d] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+__global__ void k_copy_cand(const uint4* src, uint4* dst, const SortCtl* sc) {
+    const unsigned long long n = sc->n;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (unsigned long long)gridDim.x * blockDim.x)
+        dst[k] = src[k];
+}
+
+size_t sort_scratch_bytes(int64_t capacity) {
+    int64_t nb = (capacity + kSortChunk - 1) / kSortChunk;
+    return 256 + sizeof(unsigned) * 256 * (size_t)std::max<int64_t>(nb, 1);
+}
+
+cudaError_t launch_sort_candidates(hs_candidate* cand, const unsigned long long* count, int64_t capacity,
+                                   hs_candidate* tmp, WsControl* ctl, cudaStream_t s) {
+    if (capacity <= 0) return cudaSuccess;
+    SortCtl* sc = reinterpret_cast<SortCtl*>(reinterpret_cast<char*>(ctl) + 64);
+    unsigned* hist = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(ctl) + kWsControlBytes);
+    const int nblocks = (int)((capacity + kSortChunk - 1) / kSortChunk);
+    k_sort_init<<<1, 32, 0, s>>>(count, capacity, sc);
+    k_sort_digits<<<std::min(nblocks * 4, 1024), kSortBlock, 0, s>>>(reinterpret_cast<const uint4*>(cand), sc);
+    uint4* a = reinterpret_cast<uint4*>(cand);
+    uint4* b = reinterpret_cast<uint4*>(tmp);
+    for (int p = 0; p < kSortPasses; ++p) {
+        k_sort_hist<<<nblocks, kSortBlock, 0, s>>>(a, sc, p, hist, nblocks);
+        k_sort_scan<<<1, 1024, 0, s>>>(sc, p, hist, 256 * nblocks);
+        k_sort_scatter<<<nblocks, kSortBlock, 0, s>>>(a, b, sc, p, hist, nblocks);
+        std::swap(a, b);
+    }
+    // an odd number of passes leaves the result in tmp
+    k_copy_cand<<<std::min(nblocks * 4, 1024), 256, 0, s>>>(a, reinterpret_cast<uint4*>(cand), sc);
+    return cudaGetLastError();
+}
+
+}  // namespace hs

@@ -1,0 +1,106 @@
+"""The C ABI without a GPU: the library loads, exports every entry point the header declares, and
+its host-side validation rejects bad arguments before touching the device."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "harmonic_sum.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("hs_plan_create", "hs_sum_1d", "hs_sum_2d", "hs_sum_batched", "hs_backward", "hs_plan_destroy",
+              "hs_sync_status", "hs_status_string"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(hs_lib):
+    lib = ctypes.CDLL(hs_lib.LIBRARY_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(hs_lib):
+    for s in (0, 1, 2, 3, 4, 5, 6, 100):
+        assert hs_lib.hs_status_string(s).startswith("HS_")
+    assert hs_lib.hs_version() >= 100
+
+
+@pytest.mark.parametrize("bad", [dict(variants=0), dict(variants=16), dict(hmax=0), dict(hmax=33),
+                                 dict(dtype=3), dict(max_bins=-1), dict(max_bins=(1 << 26) + 1),
+                                 dict(nz=5, z_min=1, hmax=16), dict(nz=5, z_min=-5, hmax=16),
+                                 dict(nz=5, z_min=-2, hmax=17), dict(cand_capacity=-1), dict(flags=8),
+                                 dict(threshold=float("nan"))])
+def test_plan_create_rejects(hs_lib, bad):
+    kw = dict(variants=0xF, hmax=32, dtype=0, max_bins=1 << 20, nz=0, z_min=0, threshold=6.0, cand_capacity=0,
+              flags=0)
+    kw.update(bad)
+    with pytest.raises(hs_lib.HSError) as e:
+        hs_lib.hs_plan_create(**kw)
+    assert e.value.status == hs_lib.ERR_INVALID
+
+
+def test_plan_accepts_and_sizes_workspace(hs_lib):
+    p, _ = hs_lib.hs_plan_create(cand_capacity=1 << 20)
+    a = hs_lib.hs_plan_workspace_size(p, 1)
+    b = hs_lib.hs_plan_workspace_size(p, 100000)
+    assert a % 256 == 0 and b % 256 == 0 and b >= 8 * 100000
+    hs_lib.hs_plan_destroy(p)
+
+
+def test_calls_validate_before_device_work(hs_lib):
+    lib = hs_lib._lib
+    p, _ = hs_lib.hs_plan_create(variants=hs_lib.FBIN)
+    out = hs_lib.Out()
+    # null plan, variant not in plan, null input, misaligned input, null outputs, null workspace
+    assert lib.hs_sum_1d(None, 4, 16, 10, 0, ctypes.byref(out), 256, 4096, None) == hs_lib.ERR_INVALID
+    assert lib.hs_sum_1d(p, 2, 16, 10, 0, ctypes.byref(out), 256, 4096, None) == hs_lib.ERR_INVALID
+    assert lib.hs_sum_1d(p, 4, None, 10, 0, ctypes.byref(out), 256, 4096, None) == hs_lib.ERR_INVALID
+    assert lib.hs_sum_1d(p, 4, 18, 10, 0, ctypes.byref(out), 256, 4096, None) == hs_lib.ERR_ALIGN
+    assert lib.hs_sum_1d(p, 4, 16, 10, 0, ctypes.byref(out), 256, 4096, None) == hs_lib.ERR_INVALID
+    out2 = hs_lib.Out(256, 512, None, None, None, None)
+    assert lib.hs_sum_1d(p, 4, 16, 10, 0, ctypes.byref(out2), None, 4096, None) == hs_lib.ERR_INVALID
+    assert lib.hs_sum_1d(p, 4, 16, 10, 0, ctypes.byref(out2), 256, 16, None) == hs_lib.ERR_NOMEM
+    assert lib.hs_sum_1d(p, 4, 16, -1, 0, ctypes.byref(out2), 256, 4096, None) == hs_lib.ERR_INVALID
+    # all-H table needs the plan flag; candidates need a capacity
+    out3 = hs_lib.Out(256, 512, None, 1024, None, None)
+    assert lib.hs_sum_1d(p, 4, 16, 10, 0, ctypes.byref(out3), 256, 4096, None) == hs_lib.ERR_INVALID
+    out4 = hs_lib.Out(256, 512, None, None, 2048, 4096)
+    assert lib.hs_sum_1d(p, 4, 16, 10, 0, ctypes.byref(out4), 256, 4096, None) == hs_lib.ERR_INVALID
+    # 2-D on a 1-D plan, greedy backward without a path
+    assert lib.hs_sum_2d(p, 16, 10, 10, 0, None, 256, 4096, None) == hs_lib.ERR_INVALID
+    pg, _ = hs_lib.hs_plan_create(variants=hs_lib.GREEDY)
+    assert lib.hs_backward(pg, 8, 16, None, 1, 10, 256, 512, None, 1024, None) == hs_lib.ERR_INVALID
+    hs_lib.hs_plan_destroy(p)
+    hs_lib.hs_plan_destroy(pg)
+
+
+def test_library_noise_calibration_matches_oracle(hs_lib):
+    for v in ("std", "max", "fbin", "greedy"):
+        mu, isig = hs_lib.hs_noise_calibration(v, 32)
+        omu, oisig = oracle.noise_calibration(v, 32)
+        np.testing.assert_array_equal(mu, omu)
+        np.testing.assert_array_equal(isig, oisig)
+
+
+def test_set_calibration_rejects_nonfinite(hs_lib):
+    p, _ = hs_lib.hs_plan_create()
+    mu = np.zeros(33, np.float32)
+    isig = np.ones(33, np.float32)
+    isig[5] = np.inf
+    with pytest.raises(hs_lib.HSError):
+        hs_lib.hs_plan_set_calibration(p, "max", mu, isig)
+    hs_lib.hs_plan_set_calibration(p, "max", None, None)
+    hs_lib.hs_plan_destroy(p)

@@ -1,0 +1,324 @@
+"""GPU path against the CPU oracle, through the C ABI.
+
+FP32 results (snr bits, best H, the Eq. 4 path, the every-H table, the candidate set) must equal
+the oracle's FP32 mode bit for bit; FP16/BF16 storage must equal the FP32 oracle run on the widened
+values bit for bit.  Sizes span several tiles and a ragged tail; full-size workloads are checked on
+sampled bins the oracle evaluates one by one, plus properties that hold at any size.
+"""
+import numpy as np
+import pytest
+
+import hs_synth
+import oracle
+
+from conftest import gpu_available
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not gpu_available(), reason="needs a CUDA GPU")]
+
+VARIANTS = ["std", "max", "fbin", "greedy"]
+THR = 6.0
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+
+    return t
+
+
+def _calib(variant, calibrated):
+    return oracle.noise_calibration(variant, 32) if calibrated else (None, None)
+
+
+def _make(hs_mod, variant, calibrated, dtype=0, max_bins=1 << 22, cap=1 << 16, flags=1, max_spectra=1, hmax=32):
+    hs = hs_mod.HarmonicSum(variants=hs_mod.VARIANTS[variant], hmax=hmax, dtype=dtype, max_bins=max_bins,
+                            threshold=THR, cand_capacity=cap, flags=flags, max_spectra=max_spectra)
+    mu, isig = _calib(variant, calibrated)
+    if mu is not None:
+        hs.set_calibration(variant, mu, isig)
+    return hs, mu, isig
+
+
+def _widen(torch, x_np, dtype):
+    """Store as FP16/BF16 (round to nearest even) and return (device tensor, widened float32 copy)."""
+    t = torch.from_numpy(x_np)
+    if dtype == "f16":
+        s = t.to(torch.float16)
+    elif dtype == "bf16":
+        s = t.to(torch.bfloat16)
+    else:
+        s = t
+    return s.cuda(), s.float().numpy()
+
+
+def _check_candidates(hs_mod, o, best_snr, best_h, spectrum_offsets=None, first_id=0):
+    cands = hs_mod.read_candidates(o)
+    exp = np.nonzero(best_snr > THR)[0]
+    assert int(o["cand_count"].item()) == exp.size
+    assert cands.size == exp.size
+    if spectrum_offsets is None:
+        got = np.sort(cands["bin"].astype(np.int64))
+        np.testing.assert_array_equal(got, exp)
+        order = np.argsort(cands["bin"])
+        np.testing.assert_array_equal(cands["snr"][order], best_snr[exp])
+        np.testing.assert_array_equal(cands["h"][order], best_h[exp])
+    else:
+        glob = spectrum_offsets[cands["spectrum"].astype(np.int64) - first_id] + cands["bin"].astype(np.int64)
+        order = np.argsort(glob)
+        np.testing.assert_array_equal(glob[order], exp)
+        np.testing.assert_array_equal(cands["snr"][order], best_snr[exp])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("calibrated", [False, True])
+def test_1d_pulsar_spectrum_bit_exact(hs_lib, torch, variant, calibrated):
+    x, _ = hs_synth.spectrum_1d_pulsar()
+    hs, mu, isig = _make(hs_lib, variant, calibrated)
+    o = hs.sum_1d(variant, torch.from_numpy(x).cuda(), all_h=True)
+    torch.cuda.synchronize()
+    assert hs.sync_status() == hs_lib.OK
+    r = oracle.hs_1d(variant, x, hmax=32, mu=mu, isig=isig, all_h=True, nthreads=8)
+    np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    if variant == "greedy":
+        np.testing.assert_array_equal(o["path"].cpu().numpy().view(np.uint32), r["path"])
+    _check_candidates(hs_lib, o, r["best_snr"], r["best_h"])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n_bins", [1, 2, 3, 31, 33, 257, 1000, 4097, 65536 + 13, 300001])
+def test_1d_ragged_sizes_bit_exact(hs_lib, torch, variant, n_bins):
+    x = hs_synth.spectrum(77, n_bins, n_bins)
+    hs, mu, isig = _make(hs_lib, variant, True)
+    o = hs.sum_1d(variant, torch.from_numpy(x).cuda(), all_h=True)
+    r = oracle.hs_1d(variant, x, hmax=32, mu=mu, isig=isig, all_h=True, nthreads=8)
+    np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    if variant == "greedy":
+        np.testing.assert_array_equal(o["path"].cpu().numpy().view(np.uint32), r["path"])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("hmax", [1, 7, 16])
+def test_1d_smaller_hmax(hs_lib, torch, variant, hmax):
+    x = hs_synth.spectrum(78, 0, 20000)
+    hs, _, _ = _make(hs_lib, variant, False, hmax=hmax)
+    o = hs.sum_1d(variant, torch.from_numpy(x).cuda(), all_h=True)
+    r = oracle.hs_1d(variant, x, hmax=hmax, all_h=True)
+    np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_1d_reduced_precision_bit_exact(hs_lib, torch, variant, dtype):
+    x, _ = hs_synth.spectrum_1d_pulsar()
+    xd, xw = _widen(torch, x, dtype)
+    hs, mu, isig = _make(hs_lib, variant, True, dtype={"f16": 1, "bf16": 2}[dtype])
+    o = hs.sum_1d(variant, xd, all_h=True)
+    r = oracle.hs_1d(variant, xw, hmax=32, mu=mu, isig=isig, all_h=True, nthreads=8)
+    np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+
+
+def test_special_inputs(hs_lib, torch):
+    """Constant spectra (ties everywhere: smallest H, left bins), zeros, spikes."""
+    for x in (np.zeros(5000, np.float32), np.full(5000, 1.5, np.float32), np.full(5000, -2.0, np.float32)):
+        x = x.copy()
+        x[1234] = 40.0
+        for v in VARIANTS:
+            hs, _, _ = _make(hs_lib, v, False)
+            o = hs.sum_1d(v, torch.from_numpy(x).cuda(), all_h=True)
+            r = oracle.hs_1d(v, x, all_h=True)
+            np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+            np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+            if v == "greedy":
+                np.testing.assert_array_equal(o["path"].cpu().numpy().view(np.uint32), r["path"])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batched_uneven_bit_exact(hs_lib, torch, variant):
+    lens = [0, 1, 5, 4096, 100003 - 3, 65536, 8, 0, 250000, 12]
+    lens = [(l + 3) // 4 * 4 for l in lens]  # keep every spectrum 16-byte aligned
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    x = hs_synth.batch(91, offsets)
+    hs, mu, isig = _make(hs_lib, variant, True, flags=0, max_spectra=len(lens))
+    o = hs.sum_batched(variant, torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda(), first_id=100)
+    assert hs.sync_status() == hs_lib.OK
+    r = oracle.hs_batched(variant, x, offsets, mu=mu, isig=isig, nthreads=8)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    if variant == "greedy":
+        np.testing.assert_array_equal(o["path"].cpu().numpy().view(np.uint32), r["path"])
+    _check_candidates(hs_lib, o, r["best_snr"], r["best_h"], offsets, first_id=100)
+
+
+def test_batched_bad_layout_is_reported(hs_lib, torch):
+    offsets = np.array([0, 1000, 999, 3000], np.int64)  # a negative length
+    x = torch.zeros(4000, device="cuda")
+    hs, _, _ = _make(hs_lib, "fbin", False, flags=0, max_spectra=3)
+    hs.sum_batched("fbin", x, torch.from_numpy(offsets).cuda())
+    with pytest.raises(hs_lib.HSError) as e:
+        hs.sync_status()
+    assert e.value.status == hs_lib.ERR_INVALID
+
+
+def test_candidate_overflow_reports_true_count(hs_lib, torch):
+    x = hs_synth.spectrum(5, 0, 200000)
+    hs, _, _ = _make(hs_lib, "fbin", False, cap=8)
+    o = hs.sum_1d("fbin", torch.from_numpy(x).cuda())
+    assert hs.sync_status() == hs_lib.WARN_CAND_OVERFLOW
+    r = oracle.hs_1d("fbin", x)
+    assert int(o["cand_count"].item()) == int((r["best_snr"] > THR).sum())
+    c = hs_lib.read_candidates(o)
+    assert c.size == 8
+    assert (r["best_snr"][c["bin"]] == c["snr"]).all()
+
+
+def test_graph_replay_matches_direct(hs_lib, torch):
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(24, lengths=(1 << 14, 1 << 15, 1 << 16))
+    x = hs_synth.batch(seed, offsets, pulsars)
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda()
+    hs = hs_lib.HarmonicSum(variants=0xF, threshold=THR, cand_capacity=1 << 16, max_spectra=24)
+    outs, structs = [], []
+    for v in VARIANTS:
+        o = hs.new_outputs(x.size, v, "cuda")
+        outs.append(o)
+        structs.append(hs.out_struct(o))
+    g = hs_lib.hs_graph_create_batched(hs.plan, 0xF, xd, od, structs, hs.ws)
+    for rep in range(2):
+        for o in outs:
+            o["cand_count"].zero_()
+        hs_lib.hs_graph_launch(g)
+        torch.cuda.synchronize()
+        for v, o in zip(VARIANTS, outs):
+            r = oracle.hs_batched(v, x, offsets, nthreads=8)
+            np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+            np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+            assert int(o["cand_count"].item()) == int((r["best_snr"] > THR).sum())
+    hs_lib.hs_graph_destroy(g)
+
+
+def test_sort_candidates(hs_lib, torch):
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(16, lengths=(1 << 16, 1 << 17))
+    x = hs_synth.batch(seed, offsets, pulsars)
+    hs = hs_lib.HarmonicSum(variants=0xF, threshold=3.0, cand_capacity=1 << 20, max_spectra=16)
+    o = hs.new_outputs(x.size, "fbin", "cuda")
+    hs.sum_batched("fbin", torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda(), out=o)
+    hs.sum_batched("max", torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda(),
+                   out={**hs.new_outputs(x.size, "max", "cuda", candidates=False), "cand": o["cand"],
+                        "cand_count": o["cand_count"]})
+    before = hs_lib.read_candidates(o).copy()
+    assert before.size > 10000
+    tmp = torch.empty_like(o["cand"])
+    hs_lib.hs_sort_candidates(o["cand"], o["cand_count"], tmp, hs.ws)
+    after = hs_lib.read_candidates(o)
+    key = np.lexsort((before["bin"], before["z"], before["spectrum"], before["variant"]))
+    np.testing.assert_array_equal(after, before[key])
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_standardize_cast_bit_exact(hs_lib, torch, dtype):
+    offsets = np.array([0, 1000, 1000, 50000, 123456], np.int64)
+    p = hs_synth.batch(12, offsets, raw=True)
+    mu = np.array([1.0, 0.5, 1.1, 0.9], np.float32)
+    sd = np.array([1.0, 2.0, 0.9, 1.3], np.float32)
+    out = torch.empty(p.size, dtype=torch.int16, device="cuda")
+    hs_lib.hs_standardize_cast(torch.from_numpy(p).cuda(), torch.from_numpy(offsets).cuda(),
+                               torch.from_numpy(mu).cuda(), torch.from_numpy(sd).cuda(),
+                               {"f16": 1, "bf16": 2}[dtype], out)
+    got = out.cpu().numpy().view(np.uint16)
+    for s in range(4):
+        a, b = offsets[s], offsets[s + 1]
+        np.testing.assert_array_equal(got[a:b], oracle.standardize_cast(p[a:b], mu[s], sd[s], dtype))
+
+
+def test_2d_bit_exact(hs_lib, torch):
+    nz, z_min, nb = 41, -20, 6000
+    plane, _ = hs_synth.fdas_plane(0, nz=nz, z_min=z_min, n_bins=nb)
+    hs = hs_lib.HarmonicSum(variants=1, hmax=16, nz=nz, z_min=z_min, max_bins=nb, threshold=THR,
+                            cand_capacity=1 << 16)
+    o = hs.sum_2d(torch.from_numpy(plane).cuda())
+    r = oracle.hs_2d(plane, z_min, hmax=16, nthreads=8)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    np.testing.assert_array_equal(o["best_snr_n"].cpu().numpy(), r["best_snr_n"])
+    np.testing.assert_array_equal(o["best_h_n"].cpu().numpy(), r["best_h_n"])
+    np.testing.assert_array_equal(o["best_z_n"].cpu().numpy().astype(np.int32), r["best_z_n"])
+    c = hs_lib.read_candidates(o)
+    exp = np.argwhere(r["best_snr"] > THR)
+    assert c.size == exp.shape[0]
+    got = np.sort((c["z"].astype(np.int64) - z_min) * nb + c["bin"])
+    np.testing.assert_array_equal(got, np.sort(exp[:, 0] * nb + exp[:, 1]))
+
+
+def test_2d_full_size_sampled(hs_lib, torch):
+    nz, z_min, nb = 201, -100, 1 << 21
+    plane, _ = hs_synth.fdas_plane(3, nz=nz, z_min=z_min, n_bins=nb)
+    hs = hs_lib.HarmonicSum(variants=1, hmax=16, nz=nz, z_min=z_min, max_bins=nb, threshold=THR,
+                            cand_capacity=1 << 22)
+    o = hs.sum_2d(torch.from_numpy(plane).cuda())
+    assert hs.sync_status() == hs_lib.OK
+    rng = np.random.default_rng(1)
+    rows = np.concatenate([rng.integers(0, nz, 3000), [0, nz - 1, 100, 100]])
+    bins = np.concatenate([rng.integers(0, nb, 3000), [nb - 1, 0, 0, nb - 1]])
+    r = oracle.hs_2d_cells(plane, z_min, rows, bins)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy()[rows, bins], r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy()[rows, bins], r["best_h"])
+    for n in [0, 1, 777, nb - 1]:
+        rr = oracle.hs_2d_cells(plane, z_min, np.arange(nz), np.full(nz, n))
+        k = int(np.argmax(rr["best_snr"]))
+        assert o["best_snr_n"][n].item() == rr["best_snr"][k]
+        assert int(o["best_z_n"][n].item()) == z_min + k
+    # candidates are exactly the cells above threshold
+    assert int(o["cand_count"].item()) == int((o["best_snr"] > THR).sum().item())
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_backward_matches_oracle_gradient(hs_lib, torch, variant):
+    n_spec, N = 64, 4096
+    offsets = np.arange(n_spec + 1, dtype=np.int64) * N
+    x = hs_synth.batch(404, offsets)
+    mu, isig = oracle.noise_calibration(variant, 32)
+    hs = hs_lib.HarmonicSum(variants=hs_lib.VARIANTS[variant], max_bins=N, threshold=THR, max_spectra=n_spec,
+                            calibration={variant: (mu, isig)})
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda()
+    o = hs.sum_batched(variant, xd, od)
+    g = torch.sigmoid(o["best_snr"] - 5.0)
+    grad = hs.backward(variant, xd, g, o["best_h"], o.get("path"), od).cpu().numpy().astype(np.float64)
+    r32 = oracle.hs_batched(variant, x, offsets, mu=mu, isig=isig)
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r32["best_h"])
+    gn = g.cpu().numpy().astype(np.float64)
+    exp = np.zeros(x.size)
+    for s in range(n_spec):
+        a, b = offsets[s], offsets[s + 1]
+        exp[a:b] = oracle.grad_1d(variant, x[a:b], gn[a:b], r32["best_h"][a:b], isig=isig.astype(np.float64))
+    # FP32 atomics in any order against an FP64 sum: relative 1e-5 of the summed magnitudes
+    np.testing.assert_allclose(grad, exp, rtol=1e-5, atol=1e-6)
+
+
+def test_autograd_function(hs_lib, torch):
+    N = 1 << 14
+    x = torch.from_numpy(hs_synth.spectrum(8, 0, N)).cuda().requires_grad_(True)
+    hs = hs_lib.HarmonicSum(variants=hs_lib.STD | hs_lib.MAX, max_bins=N, threshold=THR)
+    snr, bh = hs_lib.HarmonicSumFn.apply(x, hs, "max")
+    loss = torch.nn.functional.softplus(snr - 5).sum()
+    loss.backward()
+    g = torch.sigmoid(snr.detach() - 5)
+    ref = hs.backward("max", x.detach(), g, bh)
+    torch.testing.assert_close(x.grad, ref)
+
+
+def test_autotune_keeps_results(hs_lib, torch):
+    N = 1 << 20
+    x = hs_synth.spectrum(13, 0, N)
+    hs = hs_lib.HarmonicSum(variants=0xF, max_bins=N, threshold=THR)
+    scratch = torch.empty(N * 4 + N * 9 + 4096, dtype=torch.uint8, device="cuda")
+    scratch[: N * 4].view(torch.float32).copy_(torch.from_numpy(x))
+    for v in VARIANTS:
+        hs_lib.hs_autotune(hs.plan, v, N, scratch, hs.ws)
+        o = hs.sum_1d(v, torch.from_numpy(x).cuda())
+        r = oracle.hs_1d(v, x, nthreads=8)
+        np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])

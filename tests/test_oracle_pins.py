@@ -477,3 +477,20 @@ def test_batched_is_per_spectrum(variant):
         r1 = oracle.hs_1d(variant, x[a:b], hmax=32)
         np.testing.assert_array_equal(rb["best_snr"][a:b], r1["best_snr"])
         np.testing.assert_array_equal(rb["best_h"][a:b], r1["best_h"])
+
+
+def test_sampled_entry_points_match_full():
+    x = rand_spectrum(3000, 41)
+    bins = np.array([0, 1, 2, 99, 1500, 2998, 2999])
+    for v in VARIANTS:
+        full = oracle.hs_1d(v, x)
+        part = oracle.hs_bins(v, x, bins)
+        np.testing.assert_array_equal(part["best_snr"], full["best_snr"][bins])
+        np.testing.assert_array_equal(part["best_h"], full["best_h"][bins])
+    plane = np.stack([rand_spectrum(700, 900 + r) for r in range(9)])
+    full = oracle.hs_2d(plane, -4)
+    rows = np.array([0, 4, 8, 3, 5])
+    bins = np.array([0, 699, 350, 1, 17])
+    part = oracle.hs_2d_cells(plane, -4, rows, bins)
+    np.testing.assert_array_equal(part["best_snr"], full["best_snr"][rows, bins])
+    np.testing.assert_array_equal(part["best_h"], full["best_h"][rows, bins])
