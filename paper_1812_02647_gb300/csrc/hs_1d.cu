@@ -1,6 +1,7 @@
 // 1-D harmonic-sum kernels: the four variants of Section 2 (Eq. 1-4), one spectrum per launch or a
 // packed batch of spectra walked by one persistent launch over a (spectrum, tile) work queue.
 #include <algorithm>
+#include <utility>
 
 #include "hs_common.cuh"
 
@@ -14,76 +15,217 @@ namespace hs {
 template <int V, typename T>
 struct Bin;
 
-// Eq. 1: a fresh sum of x(round-half-up(n*i/H)) for every H; every index is <= n.
+// Eq. 1.  The index of harmonic i of H at output bin n, round-half-up(n*i/H), depends only on the
+// reduced fraction i/H, so each of the 324 distinct fractions of F_32 (the Farey sequence of order
+// 32) is read once and added to every S_H it belongs to.  Visiting the fractions in increasing
+// order adds the terms of each S_H in the order i = 1..H, as the definition does.
+struct Frac {
+    int p, q;
+};
+__host__ __device__ constexpr Frac farey_at(int k) {  // k-th term of F_32 after 0/1: 1/32, 1/31, ..., 1/1
+    Frac a{0, 1}, b{1, 32};
+    for (int i = 0; i < k; ++i) {
+        int m = (32 + a.q) / b.q;
+        Frac c{m * b.p - a.p, m * b.q - a.q};
+        a = b;
+        b = c;
+    }
+    return b;
+}
+constexpr int kNumFrac = 324;
+static_assert(farey_at(kNumFrac - 1).p == 1 && farey_at(kNumFrac - 1).q == 1, "F_32 has 324 terms after 0/1");
+
+// round-half-up(n*p/q) = floor((n*F + 2^31) / 2^32) with F = ceil(2^32 p/q): the error n*(F - 2^32 p/q)
+// / 2^32 < 2^-6 <= 1/(2q) for n < 2^26 never reaches the next multiple of 1/(2q), so this is exact.
+// It is evaluated in 32-bit pieces: high word of n*F plus the carry of (low word + 2^31).
+template <int P, int Q>
+struct FracConst {
+    static constexpr uint32_t F = (uint32_t)((((uint64_t)P << 32) + Q - 1) / Q);
+};
+
+template <int P, int Q>
+__device__ __forceinline__ uint32_t frac_index(uint32_t n) {
+    if (Q == 1) return n;
+    constexpr uint32_t F = FracConst<P, Q>::F;
+    return __umulhi(n, F) + ((n * F) >> 31);
+}
+
+template <typename T>
+__device__ __forceinline__ const T* elem_ptr(const T* x, uint32_t i) {
+    return x + i;
+}
+
+// Two FP32 sums per instruction: each half is rounded exactly as a separate add would be.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 r;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(*reinterpret_cast<unsigned long long*>(&r))
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return r;
+}
+
+// Generic hmax: one output per call, harmonics beyond hmax skipped.
+template <typename T, int K>
+__device__ __forceinline__ void farey_step(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1]) {
+    constexpr Frac f = farey_at(K);
+    const float v = widen<T>(__ldg(elem_ptr(x, frac_index<f.p, f.q>(n))));
+#pragma unroll
+    for (int m = 1; m * f.q <= kHmax; ++m)
+        if (m * f.q <= hmax) S[m * f.q] = __fadd_rn(S[m * f.q], v);
+}
+
+template <typename T, int... K>
+__device__ __forceinline__ void farey_all(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1],
+                                          std::integer_sequence<int, K...>) {
+    (farey_step<T, K>(x, n, hmax, S), ...);  // in increasing fraction order
+}
+
+// hmax = 32, outputs n and n+1 together.  For fraction f <= 1 their bins differ by 0 or 1: with
+// W = n*F + 2^31, bin(n) = W >> 32 and bin(n+1) = (W + F) >> 32, which is one more exactly when
+// the low word of W carries on adding F.  Both candidates are loaded and the carry picks one.
+template <typename T, int K>
+__device__ __forceinline__ void farey_pair_step(const T* x, uint32_t n, float2 (&S)[kHmax + 1]) {
+    constexpr Frac f = farey_at(K);
+    float2 v;
+    if (f.q == 1) {
+        const T* p = x + n;
+        v.x = widen<T>(__ldg(p));
+        v.y = widen<T>(__ldg(p + 1));
+    } else {
+        constexpr uint32_t F = FracConst<f.p, f.q>::F;
+        const uint32_t lo = n * F;
+        const uint32_t k = __umulhi(n, F) + (lo >> 31);
+        const T* p = x + k;
+        const float a = widen<T>(__ldg(p)), b = widen<T>(__ldg(p + 1));
+        v.x = a;
+        v.y = (lo + 0x80000000u > 0xFFFFFFFFu - F) ? b : a;
+    }
+#pragma unroll
+    for (int m = 1; m * f.q <= kHmax; ++m) S[m * f.q] = add2(S[m * f.q], v);
+}
+
+template <typename T, int... K>
+__device__ __forceinline__ void farey_pair_all(const T* x, uint32_t n, float2 (&S)[kHmax + 1],
+                                               std::integer_sequence<int, K...>) {
+    (farey_pair_step<T, K>(x, n, S), ...);
+}
+
 template <typename T>
 struct Bin<HS_STD, T> {
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path) {
+        float S[kHmax + 1];
+#pragma unroll
+        for (int H = 0; H <= kHmax; ++H) S[H] = 0.f;
+        farey_all<T>(x, n, hmax, S, std::make_integer_sequence<int, kNumFrac>{});
 #pragma unroll
         for (int H = 1; H <= kHmax; ++H) {
             if (H <= hmax) {
-                float S = 0.f;
-#pragma unroll
-                for (int i = 1; i <= H; ++i) {
-                    uint32_t idx = (2u * n * (uint32_t)i + (uint32_t)H) / (2u * (uint32_t)H);
-                    S = __fadd_rn(S, ldx(x, idx));
-                }
-                float snr = calibrate(tb, S, H);
+                float snr = calibrate(tb, S[H], H);
                 if (all_h) all_h[(size_t)(H - 1) * all_stride + n] = snr;
                 keep_best(snr, H, best, bh);
             }
         }
     }
+    // outputs n and n+1 (both < N); hmax == 32; no every-H table
+    static __device__ __forceinline__ void eval_pair(const T* x, uint32_t n, const Tables& tb, float& best_a,
+                                                     int& bh_a, float& best_b, int& bh_b) {
+        float2 S[kHmax + 1];
+#pragma unroll
+        for (int H = 0; H <= kHmax; ++H) S[H] = make_float2(0.f, 0.f);
+        farey_pair_all<T>(x, n, S, std::make_integer_sequence<int, kNumFrac>{});
+#pragma unroll
+        for (int H = 1; H <= kHmax; ++H) {
+            keep_best(calibrate(tb, S[H].x, H), H, best_a, bh_a);
+            keep_best(calibrate(tb, S[H].y, H), H, best_b, bh_b);
+        }
+    }
 };
 
-// Eq. 2: harmonic i adds the largest of x(i*n+1) .. x(i*n+i) (first maximum).
+// Largest of the elements [w0, w1] (inclusive, w0 <= w1 <= N-1), read in aligned 16-byte chunks so a
+// window of i bins costs about i/4 + 1 loads.  The maximum is exact, so the order of comparison does
+// not change its value (and inputs carry no NaN).
+template <typename T>
+__device__ __forceinline__ float window_max(const T* x, uint32_t N, uint32_t w0, uint32_t w1) {
+    constexpr uint32_t E = 16 / sizeof(T);  // elements per chunk
+    const uint32_t c0 = w0 / E, c1 = w1 / E;
+    if (c1 >= N / E) {  // the window reaches the partial chunk at the end: plain loads
+        float m = -INFINITY;
+        for (uint32_t k = w0; k <= w1; ++k) m = fmaxf(m, ldx(x, k));
+        return m;
+    }
+    const uint4* cx = reinterpret_cast<const uint4*>(x);
+    float m = -INFINITY;
+    {
+        uint4 raw = __ldg(cx + c0);
+        const T* e = reinterpret_cast<const T*>(&raw);
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k) {
+            uint32_t pos = c0 * E + k;
+            if (pos >= w0 && pos <= w1) m = fmaxf(m, widen<T>(e[k]));
+        }
+    }
+    for (uint32_t c = c0 + 1; c < c1; ++c) {
+        uint4 raw = __ldg(cx + c);
+        const T* e = reinterpret_cast<const T*>(&raw);
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k) m = fmaxf(m, widen<T>(e[k]));
+    }
+    if (c1 > c0) {
+        uint4 raw = __ldg(cx + c1);
+        const T* e = reinterpret_cast<const T*>(&raw);
+#pragma unroll
+        for (uint32_t k = 0; k < E; ++k)
+            if (c1 * E + k <= w1) m = fmaxf(m, widen<T>(e[k]));
+    }
+    return m;
+}
+
+// Eq. 2: harmonic i adds the largest of x(i*n+1) .. x(i*n+i).
 template <typename T>
 struct Bin<HS_MAX, T> {
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path) {
-        int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
+        const int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
         float S = 0.f;
-#pragma unroll 1
-        for (int i = 1; i <= hmax; ++i) {
-            float snr = -INFINITY;
-            if (i <= hv) {
-                uint32_t base = (uint32_t)i * n;
-                float m = ldx(x, base + 1);
-                for (int j = 2; j <= i; ++j) {
-                    float v = ldx(x, base + j);
-                    m = (v > m) ? v : m;
-                }
-                S = __fadd_rn(S, m);
-                snr = calibrate(tb, S, i);
-                keep_best(snr, i, best, bh);
-            }
+        for (int i = 1; i <= hv; ++i) {
+            const uint32_t base = (uint32_t)i * n;
+            S = __fadd_rn(S, window_max(x, N, base + 1, base + (uint32_t)i));
+            const float snr = calibrate(tb, S, i);
+            keep_best(snr, i, best, bh);
             if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
         }
+        if (all_h)
+            for (int i = hv + 1; i <= hmax; ++i) all_h[(size_t)(i - 1) * all_stride + n] = -INFINITY;
     }
 };
 
-// Eq. 3: harmonic i adds x(i*n).
+// Eq. 3: harmonic i adds x(i*n).  Harmonics run up to the bin's own valid count, four loads at a time.
 template <typename T>
 struct Bin<HS_FBIN, T> {
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path) {
-        int hv = (n == 0) ? hmax : (int)min((uint32_t)hmax, (N - 1) / n);
+        const int hv = (n == 0) ? hmax : (int)min((uint32_t)hmax, (N - 1) / n);
         float S = 0.f;
+        for (int i0 = 1; i0 <= hv; i0 += 4) {
+            float v[4];
 #pragma unroll
-        for (int i = 1; i <= kHmax; ++i) {
-            if (i <= hmax) {
-                float snr = -INFINITY;
-                if (i <= hv) {
-                    S = __fadd_rn(S, ldx(x, (uint32_t)i * n));
-                    snr = calibrate(tb, S, i);
-                    keep_best(snr, i, best, bh);
+            for (int k = 0; k < 4; ++k) v[k] = (i0 + k <= hv) ? ldx(x, (uint32_t)(i0 + k) * n) : 0.f;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (i0 + k <= hv) {
+                    S = __fadd_rn(S, v[k]);
+                    const float snr = calibrate(tb, S, i0 + k);
+                    keep_best(snr, i0 + k, best, bh);
+                    if (all_h) all_h[(size_t)(i0 + k - 1) * all_stride + n] = snr;
                 }
-                if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
             }
         }
+        if (all_h)
+            for (int i = hv + 1; i <= hmax; ++i) all_h[(size_t)(i - 1) * all_stride + n] = -INFINITY;
     }
 };
 
@@ -94,30 +236,22 @@ struct Bin<HS_GREEDY, T> {
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path) {
-        int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
+        const int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
         float S = 0.f;
         uint32_t j = 0, p = 0;
-#pragma unroll
-        for (int i = 1; i <= kHmax; ++i) {
-            if (i <= hmax) {
-                float snr = -INFINITY;
-                if (i <= hv) {
-                    uint32_t b = (uint32_t)i * n + j;
-                    float l = ldx(x, b), r = ldx(x, b + 1), t;
-                    if (r > l) {
-                        t = r;
-                        p |= 1u << (i - 1);
-                        j += 1;
-                    } else {
-                        t = l;
-                    }
-                    S = __fadd_rn(S, t);
-                    snr = calibrate(tb, S, i);
-                    keep_best(snr, i, best, bh);
-                }
-                if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
-            }
+        for (int i = 1; i <= hv; ++i) {
+            const uint32_t b = (uint32_t)i * n + j;
+            const float l = ldx(x, b), r = ldx(x, b + 1);
+            const bool right = r > l;
+            p |= (right ? 1u : 0u) << (i - 1);
+            j += right ? 1u : 0u;
+            S = __fadd_rn(S, right ? r : l);
+            const float snr = calibrate(tb, S, i);
+            keep_best(snr, i, best, bh);
+            if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
         }
+        if (all_h)
+            for (int i = hv + 1; i <= hmax; ++i) all_h[(size_t)(i - 1) * all_stride + n] = -INFINITY;
         path = p;
     }
 };
@@ -129,7 +263,26 @@ template <int V, typename T>
 __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, uint32_t t1, const Tables& tb,
                                          const Work1d& w, const Out1d& o, size_t out_off, uint32_t spec,
                                          unsigned* status) {
-    for (uint32_t base = t0; base < t1; base += kBlock) {
+    uint32_t base = t0;
+    if (V == HS_STD && w.hmax == kHmax && o.all_h == nullptr) {
+        // consecutive output pairs: thread t owns bins base + 2t and base + 2t + 1
+        for (; base + 2 * kBlock <= t1; base += 2 * kBlock) {
+            const uint32_t n = base + 2 * threadIdx.x;
+            float ba = -INFINITY, bb = -INFINITY;
+            int ha = 0, hb = 0;
+            Bin<HS_STD, T>::eval_pair(x, n, tb, ba, ha, bb, hb);
+            o.best_snr[out_off + n] = ba;
+            o.best_h[out_off + n] = (uint8_t)ha;
+            o.best_snr[out_off + n + 1] = bb;
+            o.best_h[out_off + n + 1] = (uint8_t)hb;
+            if (o.cand) {
+                append_candidate(ba > w.threshold, o.cand, o.cand_count, o.cand_cap, status, spec, n, ba, 0, ha, V);
+                append_candidate(bb > w.threshold, o.cand, o.cand_count, o.cand_cap, status, spec, n + 1, bb, 0, hb,
+                                 V);
+            }
+        }
+    }
+    for (; base < t1; base += kBlock) {
         uint32_t n = base + threadIdx.x;
         bool active = n < t1;
         float best = -INFINITY;
@@ -147,9 +300,28 @@ __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, ui
     }
 }
 
+template <int V>
+struct MinBlocks {
+    static constexpr int value = V == HS_STD ? 2 : 6;
+};
+
+// Eq. 2-4 index the calibration tables by a runtime H, which is cheaper from shared memory than
+// from the kernel-parameter bank; Eq. 1 unrolls H and reads the parameter bank directly.
+template <int V>
+__device__ __forceinline__ const Tables& stage_tables(const Tables& tb, Tables& smem) {
+    if (V == HS_STD) return tb;
+    for (int k = threadIdx.x; k < 3 * (kHmax + 1); k += blockDim.x)
+        reinterpret_cast<float*>(&smem)[k] = reinterpret_cast<const float*>(&tb)[k];
+    __syncthreads();
+    return smem;
+}
+
 template <int V, typename T>
-__global__ void __launch_bounds__(kBlock) k_hs1d_single(const __grid_constant__ Tables tb, const Work1d w,
-                                                        const Out1d o, WsControl* ctl) {
+__global__ void __launch_bounds__(kBlock, MinBlocks<V>::value) k_hs1d_single(const __grid_constant__ Tables tb_param,
+                                                                            const Work1d w, const Out1d o,
+                                                                            WsControl* ctl) {
+    __shared__ Tables s_tb;
+    const Tables& tb = stage_tables<V>(tb_param, s_tb);
     uint32_t N = (uint32_t)w.n_bins;
     uint32_t tile = (uint32_t)(kBlock * w.opt);
     uint32_t t0 = blockIdx.x * tile;
@@ -210,39 +382,52 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int64_t* offsets, int 
     }
 }
 
+// Last spectrum s with prefix[s] <= item (spectra with no tiles are skipped over).
+__device__ __forceinline__ int find_spectrum(const int64_t* prefix, int n_spectra, unsigned long long item) {
+    int lo = 0, hi = n_spectra - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if ((unsigned long long)__ldg(prefix + mid) <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Persistent kernel: CTAs pop (spectrum, tile) items in order from the queue.  The next item is
+// claimed while the current one is processed, so the atomic's round trip is off the critical path.
 template <int V, typename T>
-__global__ void __launch_bounds__(kBlock) k_hs1d_batched(const __grid_constant__ Tables tb, const Work1d w,
-                                                         const Out1d o, WsControl* ctl, const int64_t* prefix) {
+__global__ void __launch_bounds__(kBlock, MinBlocks<V>::value) k_hs1d_batched(const __grid_constant__ Tables tb_param,
+                                                                             const Work1d w, const Out1d o,
+                                                                             WsControl* ctl, const int64_t* prefix) {
+    __shared__ Tables s_tb;
+    const Tables& tb = stage_tables<V>(tb_param, s_tb);
     __shared__ unsigned long long s_item;
     __shared__ int s_spec;
     const unsigned long long total = *(volatile unsigned long long*)&ctl->total_items;
     const uint32_t tile = (uint32_t)(kBlock * w.opt);
+    if (threadIdx.x == 0) {
+        unsigned long long item = atomicAdd(&ctl->queue, 1u);
+        s_item = item;
+        s_spec = item < total ? find_spectrum(prefix, w.n_spectra, item) : 0;
+    }
+    __syncthreads();
     for (;;) {
-        if (threadIdx.x == 0) {
-            unsigned long long item = atomicAdd(&ctl->queue, 1u);
-            int s = 0;
-            if (item < total) {
-                int lo = 0, hi = w.n_spectra - 1;  // last s with prefix[s] <= item
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if ((unsigned long long)prefix[mid] <= item) lo = mid; else hi = mid - 1;
-                }
-                s = lo;
-            }
-            s_item = item;
-            s_spec = s;
-        }
-        __syncthreads();
-        unsigned long long item = s_item;
-        int s = s_spec;
-        __syncthreads();
+        const unsigned long long item = s_item;
+        const int s = s_spec;
         if (item >= total) break;
-        int64_t off = w.offsets[s];
-        uint32_t N = (uint32_t)(w.offsets[s + 1] - off);
-        uint32_t t0 = (uint32_t)(item - (unsigned long long)prefix[s]) * tile;
-        uint32_t t1 = min(N, t0 + tile);
+        unsigned long long next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(&ctl->queue, 1u);  // result consumed after the tile
+        const int64_t off = w.offsets[s];
+        const uint32_t N = (uint32_t)(w.offsets[s + 1] - off);
+        const uint32_t t0 = (uint32_t)(item - (unsigned long long)prefix[s]) * tile;
+        const uint32_t t1 = min(N, t0 + tile);
         run_tile<V, T>((const T*)w.x + off, N, t0, t1, tb, w, o, (size_t)off, w.first_id + (uint32_t)s,
                        &ctl->status);
+        __syncthreads();  // every thread has read s_item / s_spec
+        if (threadIdx.x == 0) {
+            s_item = next;
+            s_spec = next < total ? find_spectrum(prefix, w.n_spectra, next) : 0;
+        }
+        __syncthreads();
     }
 }
 

@@ -110,10 +110,10 @@ hs_status hs_plan_create(hs_plan** plan, const hs_plan_desc* d) {
             p->tab[k].isig[H] = 1.f;
         }
     }
-    p->launch[0].opt = 1;  // Eq. 1
-    p->launch[1].opt = 1;  // Eq. 2
+    p->launch[0].opt = 4;  // Eq. 1
+    p->launch[1].opt = 4;  // Eq. 2
     p->launch[2].opt = 8;  // Eq. 3
-    p->launch[3].opt = 4;  // Eq. 4
+    p->launch[3].opt = 8;  // Eq. 4
     p->sm_count = 0;
     *plan = p;
     return HS_OK;
