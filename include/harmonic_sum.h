@@ -161,6 +161,25 @@ hs_status hs_sum_batched(const hs_plan* plan, hs_variant v, const void* d_x, con
                          int n_spectra, uint32_t first_id, const hs_out* out, void* d_ws, size_t ws_bytes,
                          cudaStream_t stream);
 
+/* Same as hs_sum_batched, but without a workspace: for callers that cannot allocate device memory
+ * when they call, such as a real-time search pipeline that reserves all of its GPU memory at
+ * start-up and forbids allocation in its processing loop (an allocation there can stall or fail in
+ * the middle of an observation), or a plugin whose host application owns the device memory pool.
+ * (The paper has no counterpart to this; it is a deployment convenience.)
+ *   - Its scratch memory is an array of about 128 KiB compiled into the library; every GPU that
+ *     loads the library holds one copy until the process exits.  Nothing is allocated or freed.
+ *   - At most HS_NOALLOC_MAX_SPECTRA spectra per call; a larger n_spectra returns HS_ERR_INVALID.
+ *   - The first call on each device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls that may overlap on the GPU (different
+ *     streams, or different host threads) race and must be serialised by the caller.
+ *   - There is no status word to read back: a candidate overflow shows as *cand_count > capacity,
+ *     and a spectrum that breaks the layout contract is skipped (its outputs are not written).
+ * Outputs, inputs and their layout are exactly those of hs_sum_batched. */
+#define HS_NOALLOC_MAX_SPECTRA 16384
+hs_status hs_sum_batched_noalloc(const hs_plan* plan, hs_variant v, const void* d_x, const int64_t* d_offsets,
+                                 int n_spectra, uint32_t first_id, const hs_out* out, cudaStream_t stream);
+
 /* 2-D Eq. 1 over an FDAS plane of plan->nz rows (row r holds z = z_min + r) by n_bins bins,
  * rows row_stride elements apart (FP32 only in this build).  H = 1..hmax (<= 16). */
 hs_status hs_sum_2d(const hs_plan* plan, const void* d_plane, int64_t n_bins, int64_t row_stride,

@@ -380,3 +380,20 @@ def _make_autograd_fn():
             return g.to(x.dtype), None, None, None
 
     return _Fn
+
+
+# ----------------------------------------------------------------------------------------------
+# allocation-free batched entry point
+# ----------------------------------------------------------------------------------------------
+NOALLOC_MAX_SPECTRA = 16384
+
+_lib.hs_sum_batched_noalloc.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(Out),
+                                        _P]
+_lib.hs_sum_batched_noalloc.restype = ctypes.c_int
+
+
+def hs_sum_batched_noalloc(plan, variant, x, offsets, out: Out, first_id=0, stream=None):
+    """hs_sum_batched without a workspace, for callers that may not allocate device memory while
+    they run (the library's own fixed scratch array is used; see include/harmonic_sum.h)."""
+    return _check(_lib.hs_sum_batched_noalloc(plan, _variant(variant), _ptr(x), _ptr(offsets), offsets.numel() - 1,
+                                              first_id, ctypes.byref(out), _stream(stream)), "hs_sum_batched_noalloc")
