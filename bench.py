@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-sample-spectra", type=int, default=16)
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the FP16/BF16, adjoint and 2-D measurements reported beside the main line")
     return ap.parse_args()
 
 
@@ -135,14 +137,22 @@ def barrier(world):
 
 
 def reduce_max(x, world):
+    """Largest value over all ranks (the slowest rank's time decides a multi-GPU step)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_workload(n_spectra, rank):
+    """Weak scaling: every rank harmonic-sums its own batch of DM trials (trial index = rank), so
+    ranks share no data and need no collective on the data path."""
+    return hs_synth.batch_dm_trials_layout(n_spectra, trial=rank)
 
 
 def cpu_oracle_sample(offsets, x_host, n_sample, variants, cores, reps=1):
@@ -195,12 +205,135 @@ def run_reference(args):
     return 0
 
 
+def csrc_sha16():
+    """Hash of the library sources, to tell whether a stored ncu traffic figure is still current."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1812_02647_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def workload_config(args, offsets, variants):
     return {"workload": "batched DM-trial spectra: %d spectra, lengths uniform in {2^19..2^22} bins, FP32, "
                         "H_max=32, variants %s, persistent graph-captured launch per variant" %
                         (args.spectra, "+".join(variants)),
             "n_spectra": args.spectra, "total_bins": int(offsets[-1]), "hmax": HMAX, "variants": list(variants),
             "threshold": THR, "l2": "inputs (%.1f GB) larger than L2; no flush" % (offsets[-1] * 4 / 1e9)}
+
+
+def _noise(torch, shape, seed, dtype=None):
+    """Standardised exponential noise generated on the device (secondary workloads only)."""
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    u = torch.rand(shape, generator=g, device="cuda", dtype=torch.float32).clamp_(min=1e-30)
+    return u.log_().neg_().sub_(1.0)
+
+
+def _time_ms(torch, stream, fn, reps):
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fn()
+    stream.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def secondary(torch, hs, stream, reps=2):
+    """The batched (FP16/BF16 storage), adjoint and 2-D forms on their own workloads, each next to
+    the plain FP32 path on the same GPU.  Inputs are device-generated noise of the workload shapes."""
+    out = {}
+    # precision: 4096 spectra x 2^20 bins stored FP16 and BF16 after standardisation
+    n_s, n_b = 4096, 1 << 20
+    total = n_s * n_b
+    od = (torch.arange(n_s + 1, device="cuda", dtype=torch.int64) * n_b)
+    p = _noise(torch, (total,), 5000).add_(1.0)  # raw exponential power
+    mu = torch.ones(n_s, device="cuda")
+    sd = torch.ones(n_s, device="cuda")
+    res = {}
+    plans = {}
+    for name, code, tdt in (("f32", hs.F32, torch.float32), ("f16", hs.F16, torch.float16),
+                            ("bf16", hs.BF16, torch.bfloat16)):
+        if name == "f32":
+            x = p.sub(1.0)
+            cast_ms = None
+        else:
+            x = torch.empty(total, dtype=tdt, device="cuda")
+            cast_ms = _time_ms(torch, stream, lambda: hs.hs_standardize_cast(p, od, mu, sd, code, x, stream), reps)
+        h = hs.HarmonicSum(variants=0xF, hmax=HMAX, dtype=code, max_bins=n_b, threshold=THR, cand_capacity=1 << 24,
+                           max_spectra=n_s)
+        o = h.new_outputs(total, "greedy", "cuda")
+        per = {}
+        for v in VARIANTS:
+            mu_v, isig_v = hs.hs_noise_calibration(v, HMAX)
+            h.set_calibration(v, mu_v, isig_v)
+
+            def run(v=v):
+                o["cand_count"].zero_()
+                hs.hs_sum_batched(h.plan, v, x, od, h.out_struct(o), h.ws, 0, stream)
+
+            per[v] = _time_ms(torch, stream, run, reps)
+        step = sum(per.values())
+        res[name] = {"ms_per_step": step, "per_variant_ms": per, "value": total * HMAX / (step / 1e3),
+                     "input_bytes": total * x.element_size(), "cast_ms": cast_ms}
+        del x, o, h
+        torch.cuda.empty_cache()
+    for name in ("f16", "bf16"):
+        res[name]["speedup_vs_f32"] = res["f32"]["ms_per_step"] / res[name]["ms_per_step"]
+    out["precision"] = {"workload": "4096 spectra x 2^20 bins, standardised Exp(1) noise, all four variants",
+                        **res}
+    del p, mu, sd, od
+    torch.cuda.empty_cache()
+
+    # differentiation: 256 spectra x 2^20, Eq. 1 and Max, loss = sum softplus(snr - 5)
+    n_s, n_b = 256, 1 << 20
+    total = n_s * n_b
+    od = (torch.arange(n_s + 1, device="cuda", dtype=torch.int64) * n_b)
+    x = _noise(torch, (total,), 4000)
+    adj = {}
+    for v in ("std", "max"):
+        mu_v, isig_v = hs.hs_noise_calibration(v, HMAX)
+        h = hs.HarmonicSum(variants=hs.VARIANTS[v], max_bins=n_b, threshold=THR, max_spectra=n_s,
+                           calibration={v: (mu_v, isig_v)})
+        o = h.new_outputs(total, v, "cuda", candidates=False)
+        g = torch.empty(total, device="cuda")
+        gx = torch.empty(total, device="cuda")
+        fwd = _time_ms(torch, stream, lambda: hs.hs_sum_batched(h.plan, v, x, od, h.out_struct(o), h.ws, 0, stream),
+                       reps)
+        torch.sigmoid(o["best_snr"] - 5.0, out=g)
+
+        def bwd():
+            gx.zero_()
+            hs.hs_backward(h.plan, v, x, od, g, o["best_h"], o.get("path"), gx, stream)
+
+        b = _time_ms(torch, stream, bwd, reps)
+        adj[v] = {"forward_ms": fwd, "backward_ms": b, "backward_over_forward": b / fwd,
+                  "value_fwd_bwd": total * HMAX / ((fwd + b) / 1e3)}
+        del h, o, g, gx
+    out["adjoint"] = {"workload": "256 spectra x 2^20 bins FP32, loss = sum softplus(snr - 5)", **adj}
+    del x, od
+    torch.cuda.empty_cache()
+
+    # 2-D: 16 FDAS planes of 201 z rows x 2^21 bins, H = 1..16
+    nz, z_min, n_b, planes = 201, -100, 1 << 21, 16
+    plane = _noise(torch, (nz, n_b), 3000)
+    h = hs.HarmonicSum(variants=hs.STD, hmax=16, nz=nz, z_min=z_min, max_bins=n_b, threshold=THR,
+                       cand_capacity=1 << 24)
+    o = h.sum_2d(plane, stream=stream)
+    per_plane = _time_ms(torch, stream, lambda: (o["cand_count"].zero_(), h.sum_2d(plane, out=o, stream=stream)), reps)
+    out["fdas_2d"] = {"workload": "16 planes x 201 rows x 2^21 bins FP32, H = 1..16 (timed per plane, same plane)",
+                      "ms_per_plane": per_plane, "ms_per_16_planes": per_plane * planes,
+                      "cells_per_s": nz * n_b / (per_plane / 1e3),
+                      "harmonic_summed_cells_per_s": nz * n_b * 16 / (per_plane / 1e3)}
+    del plane, o, h
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -213,7 +346,7 @@ def main():
 
     rank, world, local = dist_setup()
     variants = tuple(args.variants.split(","))
-    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(args.spectra, trial=rank)
+    seed, offsets, pulsars = rank_workload(args.spectra, rank)
     total = int(offsets[-1])
     x_host = torch.empty(total, dtype=torch.float32, pin_memory=True)
     hs_synth.batch(seed, offsets, pulsars, out=x_host.data_ptr())
@@ -307,9 +440,36 @@ def main():
     peaks, peak_src = load_peaks()
     avg = {v: statistics.mean(per_variant[v]) for v in variants}
     dom = max(avg, key=avg.get)
-    out_bytes = 4 + 1 + (4 if dom == "greedy" else 0)
-    alg_bytes = total * (4 + out_bytes)
-    achieved = alg_bytes / (avg[dom] / 1e3) / 1e9
+    hbm_peak = peaks["hbm_gbs"]
+    # FP32 add peak: 152 SMs x 128 FP32 lanes x the maximum SM clock (one add per lane per clock;
+    # packed f32x2 adds do not raise it)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = sms * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+    def compulsory_bytes(v):
+        return total * (4 + 4 + 1 + (4 if v == "greedy" else 0))
+
+    per_roof = {}
+    for v in variants:
+        gbs = compulsory_bytes(v) / (avg[v] / 1e3) / 1e9
+        per_roof[v] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
+    traffic = None
+    try:
+        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        if tj.get("csrc_sha16") == csrc_sha16() and dom == "std":
+            traffic = tj["dram_bytes_per_bin"] * total
+    except Exception:
+        pass
+    if dom == "std":
+        # Eq. 1 performs 528 ordered FP32 adds per bin (sum_{H<=32} H); its HBM bytes are negligible
+        tf = 528.0 * total / (avg[dom] / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "hs::k_hs1d_batched<Eq. 1>", "achieved": tf, "peak": alu_peak,
+                "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock", "unit": "TFLOP/s",
+                "frac": tf / alu_peak, "traffic": traffic, "algorithmic_flops_per_launch": 528.0 * total}
+    else:
+        r = per_roof[dom]
+        roof = {**r, "kernel": "hs::k_hs1d_batched<%s>" % dom, "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes_per_launch": compulsory_bytes(dom)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
@@ -317,17 +477,18 @@ def main():
         "config": workload_config(args, offsets, variants),
         "gpu_launches": args.steps * 2 * len(variants),
         "per_variant_ms": avg,
-        "per_variant_compulsory_gbs": {v: total * (8 + 1 + (4 if v == "greedy" else 0)) / (avg[v] / 1e3) / 1e9
-                                       for v in variants},
+        "per_variant_roofline": per_roof,
         "candidates": n_cands,
-        "roofline": {"bound": "hbm", "kernel": "hs1d persistent, %s" % dom, "achieved": achieved,
-                     "peak": peaks["hbm_gbs"], "peak_source": peak_src, "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                     "algorithmic_bytes_per_launch": alg_bytes},
+        "roofline": roof,
         "clocks": clk,
     }
     if e2e:
         line["e2e"] = e2e
+    if not args.no_secondary:
+        del graphs, outs, xd
+        torch.cuda.empty_cache()
+        with torch.cuda.stream(stream):
+            line["secondary"] = secondary(torch, hs, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_s = min(args.cpu_sample_spectra, args.spectra)

@@ -309,11 +309,13 @@ struct MinBlocks {
 // from the kernel-parameter bank; Eq. 1 unrolls H and reads the parameter bank directly.
 template <int V>
 __device__ __forceinline__ const Tables& stage_tables(const Tables& tb, Tables& smem) {
-    if (V == HS_STD) return tb;
-    for (int k = threadIdx.x; k < 3 * (kHmax + 1); k += blockDim.x)
-        reinterpret_cast<float*>(&smem)[k] = reinterpret_cast<const float*>(&tb)[k];
-    __syncthreads();
-    return smem;
+    if (V != HS_STD) {
+        for (int k = threadIdx.x; k < 3 * (kHmax + 1); k += blockDim.x)
+            reinterpret_cast<float*>(&smem)[k] = reinterpret_cast<const float*>(&tb)[k];
+        __syncthreads();
+        return smem;
+    }
+    return tb;
 }
 
 template <int V, typename T>
