@@ -152,14 +152,27 @@ hs_status hs_sum_1d(const hs_plan* plan, hs_variant v, const void* d_x, int64_t 
                     const hs_out* out, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* A batch of spectra of uneven length packed back to back: spectrum s is
- * d_x[d_offsets[s] .. d_offsets[s+1]) (offsets: device int64[n_spectra+1], non-decreasing,
- * d_offsets[0] = 0, each length <= plan max_bins; d_offsets[s] * element size must keep every
- * spectrum 16-byte aligned).  One persistent launch walks a work queue of (spectrum, tile)
- * items; candidate spectrum ids are first_id + s.  hs_graph_create_batched captures this call in
- * a CUDA graph for replay. */
+ * d_x[d_offsets[s] .. d_offsets[s+1]) (offsets: device int64[n_spectra+1], absolute element indices
+ * into d_x, non-decreasing, each length <= plan max_bins, each start 16-byte aligned, i.e.
+ * d_offsets[s] * element size a multiple of 16).  Outputs are indexed by the same absolute
+ * positions, so a batch may be any slice of a larger packed array.  One persistent launch walks a
+ * work queue of (spectrum, tile) items; candidate spectrum ids are first_id + s.
+ * hs_graph_create_batched captures this call in a CUDA graph for replay. */
 hs_status hs_sum_batched(const hs_plan* plan, hs_variant v, const void* d_x, const int64_t* d_offsets,
                          int n_spectra, uint32_t first_id, const hs_out* out, void* d_ws, size_t ws_bytes,
                          cudaStream_t stream);
+
+/* A batch that lives in host memory, streamed to the device in n_chunks pieces: the copy of piece
+ * c+1 (host to device, on an internal stream) overlaps the harmonic sums of piece c (every variant
+ * bit set in variant_mask, in the order STD, MAX, FBIN, GREEDY, each writing to outs[k] for the k-th
+ * set bit) on the caller's stream.  h_x must be page-locked (cudaHostAlloc / pinned) for the copies
+ * to overlap; h_offsets is a host int64[n_spectra+1] array with h_offsets[0] = 0.  d_x (device, at
+ * least h_offsets[n_spectra] elements) and d_offsets (device int64[n_spectra+1]) are caller-owned
+ * staging buffers that receive the batch.  Everything is enqueued asynchronously; the call returns
+ * before the data has moved, so h_x must stay valid until the stream has been synchronised. */
+hs_status hs_sum_batched_host(const hs_plan* plan, int variant_mask, const void* h_x, const int64_t* h_offsets,
+                              int n_spectra, uint32_t first_id, void* d_x, int64_t* d_offsets, const hs_out* outs,
+                              int n_chunks, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Same as hs_sum_batched, but without a workspace: for callers that cannot allocate device memory
  * when they call, such as a real-time search pipeline that reserves all of its GPU memory at

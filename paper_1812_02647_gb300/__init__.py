@@ -77,6 +77,7 @@ def _load():
         "hs_graph_destroy": ([_P], I),
         "hs_autotune": ([_P, I, I64, _P, SZ, _P, SZ, _P], I),
         "hs_sync_status": ([_P, _P, _P], I),
+        "hs_sum_batched_host": ([_P, I, _P, _P, I, U32, _P, _P, _P, I, _P, SZ, _P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -212,6 +213,18 @@ def hs_graph_create_batched(plan, variant_mask, x, offsets, outs, ws, first_id=0
                                         first_id, ctypes.cast(arr, _P), _ptr(ws), ws.numel(), _stream(stream),
                                         ctypes.byref(g)), "hs_graph_create_batched")
     return g
+
+
+def hs_sum_batched_host(plan, variant_mask, x_host, offsets_host, x_dev, offsets_dev, outs, ws, n_chunks=8,
+                        first_id=0, stream=None):
+    """A pinned host batch streamed to the device in pieces, copies overlapping the sums.
+    ``x_host`` is a pinned torch tensor, ``offsets_host`` a numpy int64 array (starting at 0)."""
+    offs = np.ascontiguousarray(offsets_host, dtype=np.int64)
+    arr = (Out * len(outs))(*outs)
+    return _check(_lib.hs_sum_batched_host(plan, int(variant_mask), ctypes.c_void_p(x_host.data_ptr()),
+                                           offs.ctypes.data, len(offs) - 1, first_id, _ptr(x_dev), _ptr(offsets_dev),
+                                           ctypes.cast(arr, _P), int(n_chunks), _ptr(ws), ws.numel(),
+                                           _stream(stream)), "hs_sum_batched_host")
 
 
 def hs_graph_launch(graph, stream=None):

@@ -331,9 +331,10 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<V>::value) k_hs1d_single(con
     run_tile<V, T>((const T*)w.x, N, t0, t1, tb, w, o, 0, w.first_id, &ctl->status);
 }
 
-// Tile prefix sums of a batch and reset of the work queue.  One block.  A spectrum that breaks
-// the layout contract (negative or oversized length, offsets[0] != 0, misaligned start) is given
-// zero tiles and flagged in the status word.
+// Tile prefix sums of a batch and reset of the work queue.  One block.  Offsets are absolute
+// element indices into the input (a batch may be a slice of a larger one).  A spectrum that breaks
+// the layout contract (negative or oversized length, misaligned start) is given zero tiles and
+// flagged in the status word.
 __global__ void __launch_bounds__(1024) k_tile_scan(const int64_t* offsets, int n, int64_t tile, int64_t max_bins,
                                                     int elem_bytes, int64_t* prefix, WsControl* ctl) {
     __shared__ int64_t warp_sum[32];
@@ -341,7 +342,6 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int64_t* offsets, int 
     if (threadIdx.x == 0) {
         carry = 0;
         ctl->queue = 0u;
-        if (offsets[0] != 0) atomicOr(&ctl->status, kStatusBadInput);
     }
     __syncthreads();
     for (int base = 0; base < n; base += blockDim.x) {
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int64_t* offsets, int 
         int64_t t = 0;
         if (s < n) {
             int64_t a = offsets[s], b = offsets[s + 1], len = b - a;
-            bool bad = len < 0 || len > max_bins || ((a * elem_bytes) & 15) != 0;
+            bool bad = a < 0 || len < 0 || len > max_bins || ((a * elem_bytes) & 15) != 0;
             if (bad) atomicOr(&ctl->status, kStatusBadInput);
             t = bad ? 0 : (len + tile - 1) / tile;
         }

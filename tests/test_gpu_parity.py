@@ -322,3 +322,52 @@ def test_autotune_keeps_results(hs_lib, torch):
         o = hs.sum_1d(v, torch.from_numpy(x).cuda())
         r = oracle.hs_1d(v, x, nthreads=8)
         np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+
+
+@pytest.mark.parametrize("n_chunks", [1, 3, 8])
+def test_host_batch_streamed_matches_device_batch(hs_lib, torch, n_chunks):
+    """hs_sum_batched_host (copies of piece c+1 overlapping the sums of piece c) equals
+    hs_sum_batched on the same batch, for every variant and piece count."""
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(40, lengths=(1 << 14, 1 << 15, 1 << 17))
+    total = int(offsets[-1])
+    xh = torch.empty(total, dtype=torch.float32, pin_memory=True)
+    hs_synth.batch(seed, offsets, pulsars, out=xh.data_ptr())
+    hs = hs_lib.HarmonicSum(variants=0xF, threshold=THR, cand_capacity=1 << 16, max_spectra=40)
+    for v in VARIANTS:
+        mu, isig = oracle.noise_calibration(v, 32)
+        hs.set_calibration(v, mu, isig)
+    xd = torch.empty(total, device="cuda")
+    od = torch.empty(41, dtype=torch.int64, device="cuda")
+    outs = [hs.new_outputs(total, v, "cuda") for v in VARIANTS]
+    hs_lib.hs_sum_batched_host(hs.plan, 0xF, xh, offsets, xd, od, [hs.out_struct(o) for o in outs], hs.ws,
+                               n_chunks=n_chunks, first_id=3)
+    torch.cuda.synchronize()
+    assert hs.sync_status() == hs_lib.OK
+    x_ref, od_ref = xh.cuda(), torch.from_numpy(offsets).cuda()
+    for v, o in zip(VARIANTS, outs):
+        ref = hs.sum_batched(v, x_ref, od_ref, first_id=3)
+        assert torch.equal(o["best_snr"], ref["best_snr"])
+        assert torch.equal(o["best_h"], ref["best_h"])
+        if v == "greedy":
+            assert torch.equal(o["path"], ref["path"])
+        a = np.sort(hs_lib.read_candidates(o), order=["spectrum", "bin"])
+        b = np.sort(hs_lib.read_candidates(ref), order=["spectrum", "bin"])
+        np.testing.assert_array_equal(a, b)
+
+
+def test_batch_slice_with_absolute_offsets(hs_lib, torch):
+    """A batch may be a slice of a larger packed array: offsets are absolute indices."""
+    lens = [4096, 8192, 12, 65536, 20000]
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    x = hs_synth.batch(17, offsets)
+    hs = hs_lib.HarmonicSum(variants=hs_lib.MAX, threshold=THR, flags=0, max_spectra=5)
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda()
+    full = hs.sum_batched("max", xd, od)
+    part = hs.new_outputs(x.size, "max", "cuda")
+    part["best_snr"].fill_(7.0)
+    hs.sum_batched("max", xd, od[2:], out=part)  # spectra 2..4 only
+    a = int(offsets[2])
+    assert torch.equal(part["best_snr"][a:], full["best_snr"][a:])
+    assert bool((part["best_snr"][:a] == 7.0).all())
+    assert hs.sync_status() == hs_lib.OK
