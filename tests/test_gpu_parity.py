@@ -100,6 +100,34 @@ def test_1d_ragged_sizes_bit_exact(hs_lib, torch, variant, n_bins):
 
 
 @pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("n_bins", [2, 31, 33, 100, 257, 1000, 4097, 8191, 65536 + 13, 300001, 1 << 20])
+def test_1d_fast_paths_bit_exact(hs_lib, torch, variant, n_bins):
+    """Without the every-H table the kernels take their fast paths (Eq. 1 output pairs, Eq. 2
+    warp-cooperative windows); they must still equal the oracle bit for bit."""
+    x = hs_synth.spectrum(79, n_bins, n_bins, pulsar=dict(shape=1, n_harm=20, f0=n_bins / 97.3, amp=9.0, width=1.5))
+    hs, mu, isig = _make(hs_lib, variant, True, flags=0)
+    o = hs.sum_1d(variant, torch.from_numpy(x).cuda())
+    r = oracle.hs_1d(variant, x, hmax=32, mu=mu, isig=isig, nthreads=8)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    if variant == "greedy":
+        np.testing.assert_array_equal(o["path"].cpu().numpy().view(np.uint32), r["path"])
+    _check_candidates(hs_lib, o, r["best_snr"], r["best_h"])
+
+
+@pytest.mark.parametrize("variant", ["std", "max"])
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_1d_fast_paths_reduced_precision(hs_lib, torch, variant, dtype):
+    x = hs_synth.spectrum(80, 0, 200003)
+    xd, xw = _widen(torch, x, dtype)
+    hs, mu, isig = _make(hs_lib, variant, True, dtype={"f16": 1, "bf16": 2}[dtype], flags=0)
+    o = hs.sum_1d(variant, xd)
+    r = oracle.hs_1d(variant, xw, hmax=32, mu=mu, isig=isig, nthreads=8)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("hmax", [1, 7, 16])
 def test_1d_smaller_hmax(hs_lib, torch, variant, hmax):
     x = hs_synth.spectrum(78, 0, 20000)
