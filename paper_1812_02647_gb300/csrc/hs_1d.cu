@@ -55,14 +55,6 @@ __device__ __forceinline__ const T* elem_ptr(const T* x, uint32_t i) {
     return x + i;
 }
 
-// Two FP32 sums per instruction: each half is rounded exactly as a separate add would be.
-__device__ __forceinline__ float2 add2(float2 a, float2 b) {
-    float2 r;
-    asm("add.rn.f32x2 %0, %1, %2;"
-        : "=l"(*reinterpret_cast<unsigned long long*>(&r))
-        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
-    return r;
-}
 
 // Generic hmax: one output per call, harmonics beyond hmax skipped.
 template <typename T, int K>

@@ -2,6 +2,8 @@
 //   h(n, z)_H = H^-1/2 sum_{i=1..H} x(round(n*i/H), round(z*i/H)),  rounded half up, H = 1..16.
 // A CTA owns 32 consecutive bins and every row; warp g walks rows g, g+8, ...  Each cell's best
 // (snr, H) is written, and the per-bin best over rows is reduced in shared memory in row order.
+#include <utility>
+
 #include "hs_common.cuh"
 
 namespace hs {
@@ -55,7 +57,7 @@ struct CellAll<> {
                                                int&) {}
 };
 
-__global__ void __launch_bounds__(k2dBins* k2dGroups) k_hs2d(const __grid_constant__ Tables tb, const Work2d w,
+__global__ void __launch_bounds__(k2dBins * k2dGroups, 2) k_hs2d(const __grid_constant__ Tables tb, const Work2d w,
                                                             const hs_out2d o, long long cand_cap, WsControl* ctl) {
     __shared__ float s_snr[k2dGroups][k2dBins];
     __shared__ int s_row[k2dGroups][k2dBins];
@@ -107,11 +109,164 @@ __global__ void __launch_bounds__(k2dBins* k2dGroups) k_hs2d(const __grid_consta
     }
 }
 
+// ------------------------------------------------------------------------------------------
+// H = 1..16 fast path.  Both rounded indices of harmonic i of H depend only on the reduced fraction
+// i/H, so each of the 80 fractions of F_16 is read once per cell and added to every S_H it serves,
+// visiting fractions in increasing order (which keeps each S_H's terms in the order i = 1..H).  A
+// warp walks one row at a time, so the row index round(z*p/q) is the same for all its lanes; each
+// lane owns two neighbouring bins n, n+1, whose column indices differ by the carry of the
+// fixed-point low word (as in the 1-D Eq. 1 kernel).
+// ------------------------------------------------------------------------------------------
+struct Frac16 {
+    int p, q;
+};
+__host__ __device__ constexpr Frac16 farey16_at(int k) {  // k-th term of F_16 after 0/1: 1/16 .. 1/1
+    Frac16 a{0, 1}, b{1, 16};
+    for (int i = 0; i < k; ++i) {
+        int m = (16 + a.q) / b.q;
+        Frac16 c{m * b.p - a.p, m * b.q - a.q};
+        a = b;
+        b = c;
+    }
+    return b;
+}
+constexpr int kNumFrac16 = 80;
+static_assert(farey16_at(kNumFrac16 - 1).p == 1 && farey16_at(kNumFrac16 - 1).q == 1, "F_16 has 80 terms after 0/1");
+
+constexpr int k2dPairBins = 64;  // bins per CTA on the fast path (32 lanes x 2)
+
+
+
+// floor((2*z*p + q) / (2*q)) for any sign of z (round half up of z*p/q)
+template <int P, int Q>
+__device__ __forceinline__ int zround_frac(int z) {
+    const int a = 2 * z * P + Q;
+    return a >= 0 ? a / (2 * Q) : -((-a + 2 * Q - 1) / (2 * Q));
+}
+
+template <int K>
+__device__ __forceinline__ void farey16_pair_step(const float* plane, uint32_t stride, int z, int z_min, uint32_t n,
+                                                  uint32_t nmax, float2 (&S)[HS_HMAX_2D + 1]) {
+    constexpr Frac16 f = farey16_at(K);
+    // element offset of the row round(z*p/q) (the plane holds fewer than 2^32 elements)
+    const uint32_t roff = (uint32_t)(zround_frac<f.p, f.q>(z) - z_min) * stride;
+    float2 v;
+    if (f.q == 1) {
+        v.x = __ldg(plane + (roff + n));
+        v.y = __ldg(plane + (roff + min(n + 1u, nmax)));
+    } else {
+        constexpr uint32_t F = (uint32_t)((((uint64_t)f.p << 32) + f.q - 1) / f.q);
+        const uint32_t lo = n * F;
+        const uint32_t k = __umulhi(n, F) + (lo >> 31);
+        const float a = __ldg(plane + (roff + k)), b = __ldg(plane + (roff + min(k + 1u, nmax)));
+        v.x = a;
+        v.y = (lo + 0x80000000u > 0xFFFFFFFFu - F) ? b : a;
+    }
+#pragma unroll
+    for (int m = 1; m * f.q <= HS_HMAX_2D; ++m) S[m * f.q] = add2(S[m * f.q], v);
+}
+
+template <int... K>
+__device__ __forceinline__ void farey16_pair_all(const float* plane, uint32_t stride, int z, int z_min, uint32_t n,
+                                                 uint32_t nmax, float2 (&S)[HS_HMAX_2D + 1],
+                                                 std::integer_sequence<int, K...>) {
+    (farey16_pair_step<K>(plane, stride, z, z_min, n, nmax, S), ...);
+}
+
+__global__ void __launch_bounds__(k2dGroups * 32, 2) k_hs2d_pairs(const __grid_constant__ Tables tb, const Work2d w,
+                                                               const hs_out2d o, long long cand_cap, WsControl* ctl) {
+    __shared__ float s_snr[k2dGroups][k2dPairBins];
+    __shared__ int s_row[k2dGroups][k2dPairBins];
+    __shared__ int s_h[k2dGroups][k2dPairBins];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const uint32_t nb = (uint32_t)w.n_bins;
+    const uint32_t n = blockIdx.x * k2dPairBins + 2 * lane;  // this lane's bins n and n+1
+    const bool act0 = n < nb, act1 = n + 1 < nb;
+    const uint32_t nq = act0 ? n : nb - 1;  // keep every read inside the row
+    float rb[2] = {-INFINITY, -INFINITY};
+    int rr[2] = {0x7fffffff, 0x7fffffff}, rh[2] = {0, 0};
+    for (int r = g; r < w.nz; r += k2dGroups) {
+        const int z = w.z_min + r;
+        float2 S[HS_HMAX_2D + 1];
+#pragma unroll
+        for (int H = 0; H <= HS_HMAX_2D; ++H) S[H] = make_float2(0.f, 0.f);
+        farey16_pair_all(w.plane, (uint32_t)w.row_stride, z, w.z_min, nq, nb - 1, S,
+                         std::make_integer_sequence<int, kNumFrac16>{});
+        float b0 = -INFINITY, b1 = -INFINITY;
+        int h0 = 0, h1 = 0;
+#pragma unroll
+        for (int H = 1; H <= HS_HMAX_2D; ++H) {
+            keep_best(calibrate(tb, S[H].x, H), H, b0, h0);
+            keep_best(calibrate(tb, S[H].y, H), H, b1, h1);
+        }
+        const size_t cell = (size_t)r * nb + n;
+        if (act1) {
+            *reinterpret_cast<float2*>(o.best_snr + cell) = make_float2(b0, b1);
+            o.best_h[cell] = (uint8_t)h0;
+            o.best_h[cell + 1] = (uint8_t)h1;
+        } else if (act0) {
+            o.best_snr[cell] = b0;
+            o.best_h[cell] = (uint8_t)h0;
+        }
+        if (act0 && b0 > rb[0]) {  // rows visited in increasing order: the lowest row keeps ties
+            rb[0] = b0;
+            rr[0] = r;
+            rh[0] = h0;
+        }
+        if (act1 && b1 > rb[1]) {
+            rb[1] = b1;
+            rr[1] = r;
+            rh[1] = h1;
+        }
+        if (o.cand) {
+            append_candidate(act0 && b0 > w.threshold, o.cand, o.cand_count, cand_cap, &ctl->status, w.plane_id, n,
+                             b0, z, h0, HS_STD);
+            append_candidate(act1 && b1 > w.threshold, o.cand, o.cand_count, cand_cap, &ctl->status, w.plane_id,
+                             n + 1, b1, z, h1, HS_STD);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        s_snr[g][2 * lane + k] = rb[k];
+        s_row[g][2 * lane + k] = rr[k];
+        s_h[g][2 * lane + k] = rh[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < k2dPairBins) {
+        const int c = threadIdx.x;
+        const uint32_t nn = blockIdx.x * k2dPairBins + c;
+        if (nn < nb) {
+            float b = s_snr[0][c];
+            int br = s_row[0][c], bh = s_h[0][c];
+            for (int k = 1; k < k2dGroups; ++k) {
+                const float v = s_snr[k][c];
+                const int rw = s_row[k][c];
+                if (v > b || (v == b && rw < br)) {
+                    b = v;
+                    br = rw;
+                    bh = s_h[k][c];
+                }
+            }
+            o.best_snr_n[nn] = b;
+            o.best_h_n[nn] = (uint8_t)bh;
+            o.best_z_n[nn] = (int16_t)(w.z_min + (br == 0x7fffffff ? 0 : br));
+        }
+    }
+}
+
 cudaError_t launch_2d(const Tables& tab, const Work2d& w, const hs_out2d& o, long long cand_cap, WsControl* ctl,
                       cudaStream_t s) {
     if (w.n_bins == 0) return cudaSuccess;
-    unsigned grid = (unsigned)((w.n_bins + k2dBins - 1) / k2dBins);
-    k_hs2d<<<grid, k2dBins * k2dGroups, 0, s>>>(tab, w, o, cand_cap, ctl);
+    // float2 stores of the cell pair (n, n+1) need an even row length and an 8-byte aligned output
+    const bool cells_aligned = (w.n_bins % 2) == 0 && (reinterpret_cast<uintptr_t>(o.best_snr) & 7) == 0;
+    const bool small_plane = (uint64_t)w.nz * (uint64_t)w.row_stride < (1ull << 32);
+    if (w.hmax == HS_HMAX_2D && cells_aligned && small_plane) {
+        unsigned grid = (unsigned)((w.n_bins + k2dPairBins - 1) / k2dPairBins);
+        k_hs2d_pairs<<<grid, k2dGroups * 32, 0, s>>>(tab, w, o, cand_cap, ctl);
+    } else {
+        unsigned grid = (unsigned)((w.n_bins + k2dBins - 1) / k2dBins);
+        k_hs2d<<<grid, k2dBins * k2dGroups, 0, s>>>(tab, w, o, cand_cap, ctl);
+    }
     return cudaGetLastError();
 }
 

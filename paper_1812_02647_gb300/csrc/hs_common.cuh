@@ -41,6 +41,15 @@ __device__ __forceinline__ float calibrate(const Tables& t, float S, int H) {
     return __fmul_rn(__fsub_rn(__fmul_rn(S, t.c[H]), t.mu[H]), t.isig[H]);
 }
 
+// Two FP32 sums per instruction: each half is rounded exactly as a separate add would be.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 r;
+    asm("add.rn.f32x2 %0, %1, %2;"
+        : "=l"(*reinterpret_cast<unsigned long long*>(&r))
+        : "l"(*reinterpret_cast<unsigned long long*>(&a)), "l"(*reinterpret_cast<unsigned long long*>(&b)));
+    return r;
+}
+
 // Running best over H: replaced only on a strictly larger snr, so the smallest H wins ties.
 __device__ __forceinline__ void keep_best(float snr, int H, float& best, int& bh) {
     if (snr > best) {

@@ -282,6 +282,25 @@ def test_2d_bit_exact(hs_lib, torch):
     np.testing.assert_array_equal(got, np.sort(exp[:, 0] * nb + exp[:, 1]))
 
 
+@pytest.mark.parametrize("nb,hmax", [(3001, 16), (4000, 9), (4000, 1), (2, 16)])
+def test_2d_generic_and_edge_paths(hs_lib, torch, nb, hmax):
+    """Odd row lengths and hmax < 16 take the generic kernel; tiny rows test the edges."""
+    nz, z_min = 21, -10
+    plane, _ = hs_synth.fdas_plane(5, nz=nz, z_min=z_min, n_bins=max(nb, 64))
+    plane = np.ascontiguousarray(plane[:, :nb])
+    stride = (nb + 3) // 4 * 4  # rows 16-byte aligned, as the ABI requires
+    padded = torch.zeros((nz, stride), device="cuda")
+    padded[:, :nb] = torch.from_numpy(plane).cuda()
+    hs = hs_lib.HarmonicSum(variants=1, hmax=hmax, nz=nz, z_min=z_min, max_bins=nb, threshold=THR,
+                            cand_capacity=1 << 16)
+    o = hs.sum_2d(padded[:, :nb])
+    r = oracle.hs_2d(plane, z_min, hmax=hmax, nthreads=8)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    np.testing.assert_array_equal(o["best_snr_n"].cpu().numpy(), r["best_snr_n"])
+    np.testing.assert_array_equal(o["best_z_n"].cpu().numpy().astype(np.int32), r["best_z_n"])
+
+
 def test_2d_full_size_sampled(hs_lib, torch):
     nz, z_min, nb = 201, -100, 1 << 21
     plane, _ = hs_synth.fdas_plane(3, nz=nz, z_min=z_min, n_bins=nb)
