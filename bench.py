@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--variants", default=",".join(VARIANTS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default (or --tiles) tile sizes")
+    ap.add_argument("--tiles", default="", help="variant=bins,... tile sizes to use instead of tuning")
     ap.add_argument("--cpu-sample-spectra", type=int, default=16)
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the FP16/BF16, adjoint and 2-D measurements reported beside the main line")
@@ -361,18 +362,25 @@ def main():
         for v in variants:
             mu, isig = hs.hs_noise_calibration(v, HMAX)
             h.set_calibration(v, mu, isig)
-        if args.autotune:
-            n_t = 1 << 22
-            scratch = torch.empty(n_t * 4 + n_t * 9 + 4096, dtype=torch.uint8, device="cuda")
-            scratch[: n_t * 4].view(torch.float32).copy_(xd[:n_t])
-            for v in variants:
-                hs.hs_autotune(h.plan, v, n_t, scratch, h.ws)
-            del scratch
         outs = {v: h.new_outputs(total, v, "cuda") for v in variants}
+        tuned = {}
+        for kv in filter(None, args.tiles.split(",")):
+            v, bins = kv.split("=")
+            hs.hs_plan_set_tile_bins(h.plan, v, int(bins))
+        if not args.no_autotune and not args.tiles:
+            # tile sizes tuned on this very batch (outputs are rewritten by the timed steps)
+            for v in variants:
+                hs.hs_autotune_batched(h.plan, v, xd, od, h.out_struct(outs[v]), h.ws, stream)
+        for v in variants:
+            tuned[v] = hs.hs_plan_tile_bins(h.plan, v)
+        cand_tmp = torch.empty(cap * 16, dtype=torch.uint8, device="cuda")
         graphs = {v: hs.hs_graph_create_batched(h.plan, hs.VARIANTS[v], xd, od, [h.out_struct(outs[v])], h.ws)
                   for v in variants}
         ev = {v: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for v in variants}
         per_variant = {v: [] for v in variants}
+
+        ev_sort = {v: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for v in variants}
+        sort_ms = {v: [] for v in variants}
 
         def step(record=False):
             for v in variants:
@@ -382,10 +390,15 @@ def main():
                 hs.hs_graph_launch(graphs[v], stream)
                 if record:
                     ev[v][1].record(stream)
+                # the candidate list of the step, sorted by (variant, spectrum, z, bin) on the device
+                hs.hs_sort_candidates(outs[v]["cand"], outs[v]["cand_count"], cand_tmp, h.ws, stream)
+                if record:
+                    ev_sort[v][1].record(stream)
             if record:
                 stream.synchronize()
                 for v in variants:
                     per_variant[v].append(ev[v][0].elapsed_time(ev[v][1]))
+                    sort_ms[v].append(ev[v][1].elapsed_time(ev_sort[v][1]))
 
         for _ in range(max(args.warmup, 0)):
             step()
@@ -430,6 +443,8 @@ def main():
                     outs[v]["cand_count"].zero_()
                 hs.hs_sum_batched_host(h.plan, mask, x_host, offsets, xd, od_stage, structs, h.ws, n_chunks=8,
                                        stream=stream)
+                for v in variants:
+                    hs.hs_sort_candidates(outs[v]["cand"], outs[v]["cand_count"], cand_tmp, h.ws, stream)
                 for i, v in enumerate(variants):
                     cnt_host[i : i + 1].copy_(outs[v]["cand_count"], non_blocking=True)
                 stream.synchronize()
@@ -484,8 +499,10 @@ def main():
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": workload_config(args, offsets, variants),
-        "gpu_launches": args.steps * 2 * len(variants),
+        "gpu_launches": args.steps * (2 + 36) * len(variants),
         "per_variant_ms": avg,
+        "sort_ms": {v: statistics.mean(sort_ms[v]) for v in variants},
+        "tile_bins": tuned,
         "per_variant_roofline": per_roof,
         "candidates": n_cands,
         "roofline": roof,

@@ -242,11 +242,26 @@ hs_status hs_graph_destroy(hs_graph* graph);
 
 /* ---- tuning and status ------------------------------------------------------------------ */
 
-/* Time the launch shapes of one variant on synthetic data of n_bins bins resident in d_scratch
- * (caller-owned, >= n_bins * element size + 16 MiB of outputs) and keep the fastest in the plan;
- * results are cached in the JSON file named by HS_AUTOTUNE_CACHE (if set). */
+/* Time the tile shapes of one variant and keep the fastest in the plan.  d_scratch (caller-owned)
+ * starts with one spectrum of n_bins elements of the plan's dtype; the tuner replicates it into a
+ * batch of 8 spectra and times hs_sum_batched on it, so d_scratch must hold 8 * n_bins * (element
+ * size + 9) bytes plus 1 KiB, and the workspace must be sized for 8 spectra.  Results are cached in
+ * the JSON file named by HS_AUTOTUNE_CACHE (if set); a cached entry is used without timing. */
 hs_status hs_autotune(hs_plan* plan, hs_variant v, int64_t n_bins, void* d_scratch, size_t scratch_bytes,
                       void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Tune on the caller's own batch (same arguments as hs_sum_batched, outputs overwritten, candidates
+ * untouched): each tile shape is timed twice on exactly this work and the fastest kept in the plan.
+ * Synchronises the stream. */
+hs_status hs_autotune_batched(hs_plan* plan, hs_variant v, const void* d_x, const int64_t* d_offsets, int n_spectra,
+                              const hs_out* out, void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Output bins per work item (tile) the plan currently uses for a variant (0 for a bad argument). */
+int hs_plan_tile_bins(const hs_plan* plan, hs_variant v);
+
+/* Set the tile of a variant to tile_bins output bins (a multiple of 256, at most 16384), e.g. a value
+ * an earlier tuning run reported.  HS_ERR_INVALID otherwise. */
+hs_status hs_plan_set_tile_bins(hs_plan* plan, hs_variant v, int tile_bins);
 
 /* Synchronise the stream and return the device status word of the workspace: HS_OK,
  * HS_WARN_CAND_OVERFLOW or HS_ERR_TIMEOUT.  Also reports a pending CUDA error as HS_ERR_CUDA. */

@@ -78,6 +78,9 @@ def _load():
         "hs_autotune": ([_P, I, I64, _P, SZ, _P, SZ, _P], I),
         "hs_sync_status": ([_P, _P, _P], I),
         "hs_sum_batched_host": ([_P, I, _P, _P, I, U32, _P, _P, _P, I, _P, SZ, _P], I),
+        "hs_autotune_batched": ([_P, I, _P, _P, I, ctypes.POINTER(Out), _P, SZ, _P], I),
+        "hs_plan_tile_bins": ([_P, I], I),
+        "hs_plan_set_tile_bins": ([_P, I, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -238,6 +241,20 @@ def hs_graph_destroy(graph):
 def hs_autotune(plan, variant, n_bins, scratch, ws, stream=None):
     return _check(_lib.hs_autotune(plan, _variant(variant), int(n_bins), _ptr(scratch), scratch.numel(), _ptr(ws),
                                    ws.numel(), _stream(stream)), "hs_autotune")
+
+
+def hs_autotune_batched(plan, variant, x, offsets, out: Out, ws, stream=None):
+    return _check(_lib.hs_autotune_batched(plan, _variant(variant), _ptr(x), _ptr(offsets), offsets.numel() - 1,
+                                           ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)),
+                  "hs_autotune_batched")
+
+
+def hs_plan_tile_bins(plan, variant) -> int:
+    return _lib.hs_plan_tile_bins(plan, _variant(variant))
+
+
+def hs_plan_set_tile_bins(plan, variant, tile_bins):
+    return _check(_lib.hs_plan_set_tile_bins(plan, _variant(variant), int(tile_bins)), "hs_plan_set_tile_bins")
 
 
 def hs_sync_status(plan, ws, stream=None) -> int:

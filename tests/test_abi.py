@@ -9,6 +9,8 @@ import pytest
 
 import oracle
 
+from conftest import gpu_available
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "harmonic_sum.h")
 
@@ -103,4 +105,34 @@ def test_set_calibration_rejects_nonfinite(hs_lib):
     with pytest.raises(hs_lib.HSError):
         hs_lib.hs_plan_set_calibration(p, "max", mu, isig)
     hs_lib.hs_plan_set_calibration(p, "max", None, None)
+    hs_lib.hs_plan_destroy(p)
+
+
+@pytest.mark.skipif(gpu_available(), reason="the key names the device's SM count; with a GPU a miss would time "
+                                             "kernels on the placeholder pointers")
+def test_autotune_uses_cached_entry_without_timing(hs_lib, tmp_path, monkeypatch):
+    """Without a device the cache key has SM count 0; an entry for it is taken as is, with no device
+    work (the placeholder pointers are never used)."""
+    cache = tmp_path / "tune.json"
+    cache.write_text('{\n  "v1_d0_h32_b20_sm0": 8,\n  "v2_d0_h32_b20_sm0": 16\n}\n')
+    monkeypatch.setenv("HS_AUTOTUNE_CACHE", str(cache))
+    lib = hs_lib._lib
+    p, _ = hs_lib.hs_plan_create(variants=0xF, max_bins=1 << 20)
+    # fake device pointers: a cache hit returns before touching them
+    st = lib.hs_autotune(p, 1, 1 << 20, ctypes.c_void_p(4096), 1 << 30, ctypes.c_void_p(8192), 1 << 20, None)
+    assert st == hs_lib.OK
+    assert lib.hs_autotune(p, 2, 1 << 20, ctypes.c_void_p(4096), 1 << 30, ctypes.c_void_p(8192), 1 << 20,
+                           None) == hs_lib.OK
+    assert lib.hs_autotune(p, 1, 0, ctypes.c_void_p(4096), 1 << 30, ctypes.c_void_p(8192), 1 << 20,
+                           None) == hs_lib.ERR_INVALID
+    hs_lib.hs_plan_destroy(p)
+
+
+def test_tile_bins_round_trip(hs_lib):
+    p, _ = hs_lib.hs_plan_create()
+    hs_lib.hs_plan_set_tile_bins(p, "std", 8192)
+    assert hs_lib.hs_plan_tile_bins(p, "std") == 8192
+    for bad in (0, 100, 255, 257, 64 * 256 + 256):
+        with pytest.raises(hs_lib.HSError):
+            hs_lib.hs_plan_set_tile_bins(p, "max", bad)
     hs_lib.hs_plan_destroy(p)

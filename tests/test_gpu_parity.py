@@ -358,11 +358,28 @@ def test_autograd_function(hs_lib, torch):
     torch.testing.assert_close(x.grad, ref)
 
 
+def test_autotune_batched_keeps_results(hs_lib, torch):
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(12, lengths=(1 << 16, 1 << 18))
+    x = hs_synth.batch(seed, offsets, pulsars)
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda()
+    hs = hs_lib.HarmonicSum(variants=0xF, threshold=THR, cand_capacity=1 << 16, max_spectra=12)
+    for v in VARIANTS:
+        o = hs.new_outputs(x.size, v, "cuda")
+        hs_lib.hs_autotune_batched(hs.plan, v, xd, od, hs.out_struct(o), hs.ws)
+        assert hs_lib.hs_plan_tile_bins(hs.plan, v) in (512, 1024, 2048, 4096, 8192)
+        assert int(o["cand_count"].item()) == 0  # tuning leaves the candidate list alone
+        hs.sum_batched(v, xd, od, out=o)
+        r = oracle.hs_batched(v, x, offsets, nthreads=8)
+        np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+        np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+
+
 def test_autotune_keeps_results(hs_lib, torch):
     N = 1 << 20
     x = hs_synth.spectrum(13, 0, N)
     hs = hs_lib.HarmonicSum(variants=0xF, max_bins=N, threshold=THR)
-    scratch = torch.empty(N * 4 + N * 9 + 4096, dtype=torch.uint8, device="cuda")
+    scratch = torch.empty(8 * N * 13 + 8192, dtype=torch.uint8, device="cuda")
+    hs.ensure_workspace(8)
     scratch[: N * 4].view(torch.float32).copy_(torch.from_numpy(x))
     for v in VARIANTS:
         hs_lib.hs_autotune(hs.plan, v, N, scratch, hs.ws)
