@@ -65,6 +65,7 @@ __device__ __forceinline__ unsigned cand_digit(const uint4& c, int pass) {
 
 struct SortCtl {
     unsigned long long n;     // number of candidates to sort
+    unsigned nb;              // blocks that hold candidates: the histogram's row stride
     unsigned dig_or[kSortPasses];
     unsigned dig_and[kSortPasses];
 };
@@ -73,6 +74,7 @@ __global__ void k_sort_init(const unsigned long long* count, long long cap, Sort
     if (threadIdx.x == 0) {
         unsigned long long c = *count;
         sc->n = c < (unsigned long long)cap ? c : (unsigned long long)cap;
+        sc->nb = (unsigned)((sc->n + kSortChunk - 1) / kSortChunk);
     }
     if (threadIdx.x < kSortPasses) {
         sc->dig_or[threadIdx.x] = 0u;
@@ -108,10 +110,11 @@ __device__ __forceinline__ bool pass_skipped(const SortCtl* sc, int pass) {
 
 // per-block digit histograms, stored digit-major: hist[d * nblocks + block]
 __global__ void __launch_bounds__(kSortBlock) k_sort_hist(const uint4* src, const SortCtl* sc, int pass,
-                                                          unsigned* hist, int nblocks) {
+                                                          unsigned* hist) {
     __shared__ unsigned h[256];
-    if (pass_skipped(sc, pass)) return;
+    if (pass_skipped(sc, pass) || blockIdx.x >= sc->nb) return;
     const unsigned long long n = sc->n;
+    const unsigned nblocks = sc->nb;
     h[threadIdx.x] = 0u;
     __syncthreads();
     const unsigned long long c0 = (unsigned long long)blockIdx.x * kSortChunk;
@@ -123,17 +126,24 @@ __global__ void __launch_bounds__(kSortBlock) k_sort_hist(const uint4* src, cons
     hist[(size_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
-// exclusive scan of hist (256 * nblocks entries) in place, one block
-__global__ void __launch_bounds__(1024) k_sort_scan(const SortCtl* sc, int pass, unsigned* hist, int total) {
+// exclusive scan of hist (256 * nb entries) in place, one block; four consecutive entries per thread
+__global__ void __launch_bounds__(1024) k_sort_scan(const SortCtl* sc, int pass, unsigned* hist) {
     __shared__ unsigned ws[32];
     __shared__ unsigned carry;
     if (pass_skipped(sc, pass)) return;
+    const int total = 256 * (int)sc->nb;
     if (threadIdx.x == 0) carry = 0u;
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int base = 0; base < total; base += 1024) {
-        int i = base + threadIdx.x;
-        unsigned t = i < total ? hist[i] : 0u, v = t;
+    for (int base = 0; base < total; base += 4096) {
+        const int i0 = base + 4 * threadIdx.x;
+        unsigned e[4], t = 0u;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            e[k] = i0 + k < total ? hist[i0 + k] : 0u;
+            t += e[k];
+        }
+        unsigned v = t;
         for (int d = 1; d < 32; d <<= 1) {
             unsigned u = __shfl_up_sync(0xffffffffu, v, d);
             if (lane >= d) v += u;
@@ -149,23 +159,28 @@ __global__ void __launch_bounds__(1024) k_sort_scan(const SortCtl* sc, int pass,
             ws[lane] = x;
         }
         __syncthreads();
-        unsigned excl = carry + (wid ? ws[wid - 1] : 0u) + v - t;
-        if (i < total) hist[i] = excl;
+        unsigned run = carry + (wid ? ws[wid - 1] : 0u) + v - t;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (i0 + k < total) hist[i0 + k] = run;
+            run += e[k];
+        }
         __syncthreads();
-        if (threadIdx.x == 1023) carry = excl + t;
+        if (threadIdx.x == 1023) carry = run;
         __syncthreads();
     }
 }
 
 // stable scatter: warp w of a block owns the w-th contiguous slice of the block's chunk
 __global__ void __launch_bounds__(kSortBlock) k_sort_scatter(const uint4* src, uint4* dst, const SortCtl* sc,
-                                                             int pass, const unsigned* hist, int nblocks) {
+                                                             int pass, const unsigned* hist) {
     constexpr int kWarps = kSortBlock / 32;
     constexpr int kSlice = kSortChunk / kWarps;
     __shared__ unsigned wbase[kWarps][256];
     const unsigned long long n = sc->n;
     const unsigned long long c0 = (unsigned long long)blockIdx.x * kSortChunk;
     if (c0 >= n) return;
+    const unsigned nblocks = sc->nb;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (pass_skipped(sc, pass)) {
         for (int k = threadIdx.x; k < kSortChunk; k += kSortBlock) {
@@ -229,9 +244,9 @@ cudaError_t launch_sort_candidates(hs_candidate* cand, const unsigned long long*
     uint4* a = reinterpret_cast<uint4*>(cand);
     uint4* b = reinterpret_cast<uint4*>(tmp);
     for (int p = 0; p < kSortPasses; ++p) {
-        k_sort_hist<<<nblocks, kSortBlock, 0, s>>>(a, sc, p, hist, nblocks);
-        k_sort_scan<<<1, 1024, 0, s>>>(sc, p, hist, 256 * nblocks);
-        k_sort_scatter<<<nblocks, kSortBlock, 0, s>>>(a, b, sc, p, hist, nblocks);
+        k_sort_hist<<<nblocks, kSortBlock, 0, s>>>(a, sc, p, hist);
+        k_sort_scan<<<1, 1024, 0, s>>>(sc, p, hist);
+        k_sort_scatter<<<nblocks, kSortBlock, 0, s>>>(a, b, sc, p, hist);
         std::swap(a, b);
     }
     // an odd number of passes leaves the result in tmp
