@@ -246,7 +246,7 @@ def _time_ms(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def secondary(torch, hs, stream, reps=2):
+def secondary(torch, hs, stream, tiles=None, reps=2):
     """The batched (FP16/BF16 storage), adjoint and 2-D forms on their own workloads, each next to
     the plain FP32 path on the same GPU.  Inputs are device-generated noise of the workload shapes."""
     out = {}
@@ -269,6 +269,8 @@ def secondary(torch, hs, stream, reps=2):
             cast_ms = _time_ms(torch, stream, lambda: hs.hs_standardize_cast(p, od, mu, sd, code, x, stream), reps)
         h = hs.HarmonicSum(variants=0xF, hmax=HMAX, dtype=code, max_bins=n_b, threshold=THR, cand_capacity=1 << 24,
                            max_spectra=n_s)
+        for v, bins in (tiles or {}).items():
+            hs.hs_plan_set_tile_bins(h.plan, v, bins)
         o = h.new_outputs(total, "greedy", "cuda")
         per = {}
         for v in VARIANTS:
@@ -282,7 +284,8 @@ def secondary(torch, hs, stream, reps=2):
             per[v] = _time_ms(torch, stream, run, reps)
         step = sum(per.values())
         res[name] = {"ms_per_step": step, "per_variant_ms": per, "value": total * HMAX / (step / 1e3),
-                     "input_bytes": total * x.element_size(), "cast_ms": cast_ms}
+                     "input_bytes": total * x.element_size(), "cast_ms": cast_ms,
+                     "cast_gbs": None if cast_ms is None else total * (4 + 2) / (cast_ms / 1e3) / 1e9}
         del x, o, h
         torch.cuda.empty_cache()
     for name in ("f16", "bf16"):
@@ -302,6 +305,8 @@ def secondary(torch, hs, stream, reps=2):
         mu_v, isig_v = hs.hs_noise_calibration(v, HMAX)
         h = hs.HarmonicSum(variants=hs.VARIANTS[v], max_bins=n_b, threshold=THR, max_spectra=n_s,
                            calibration={v: (mu_v, isig_v)})
+        if tiles and v in tiles:
+            hs.hs_plan_set_tile_bins(h.plan, v, tiles[v])
         o = h.new_outputs(total, v, "cuda", candidates=False)
         g = torch.empty(total, device="cuda")
         gx = torch.empty(total, device="cuda")
@@ -514,7 +519,7 @@ def main():
         del graphs, outs, xd
         torch.cuda.empty_cache()
         with torch.cuda.stream(stream):
-            line["secondary"] = secondary(torch, hs, stream)
+            line["secondary"] = secondary(torch, hs, stream, tiles=tuned)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_s = min(args.cpu_sample_spectra, args.spectra)

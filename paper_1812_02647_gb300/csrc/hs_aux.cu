@@ -20,26 +20,67 @@ __device__ __forceinline__ __nv_bfloat16 narrow<__nv_bfloat16>(float y) {
     return __float2bfloat16_rn(y);
 }
 
+// Streaming kernel: blockIdx.y walks spectra, the x-blocks of a row stride over the spectrum with
+// 16-byte loads of four values (8-byte stores of four FP16/BF16 results); a spectrum whose start or
+// length is not a multiple of four takes the element-wise path for its head and tail.
 template <typename T>
-__global__ void __launch_bounds__(256) k_standardize_cast(const float* p, const int64_t* offsets, int64_t n_bins,
-                                                          const float* mu, const float* sigma, T* out) {
-    const int s = blockIdx.y;
-    const int64_t off = offsets ? offsets[s] : 0;
-    const int64_t N = offsets ? offsets[s + 1] - off : n_bins;
-    const float m = mu[s], sd = sigma[s];
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x)
-        out[off + k] = narrow<T>(__fdiv_rn(__fsub_rn(p[off + k], m), sd));
+struct Pack4;
+template <>
+struct Pack4<__half> {
+    static __device__ __forceinline__ uint2 make(float a, float b, float c, float d) {
+        __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+        return make_uint2(*reinterpret_cast<unsigned*>(&lo), *reinterpret_cast<unsigned*>(&hi));
+    }
+};
+template <>
+struct Pack4<__nv_bfloat16> {
+    static __device__ __forceinline__ uint2 make(float a, float b, float c, float d) {
+        __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+        return make_uint2(*reinterpret_cast<unsigned*>(&lo), *reinterpret_cast<unsigned*>(&hi));
+    }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_standardize_cast(const float* p, const int64_t* offsets, int n_spectra,
+                                                          int64_t n_bins, const float* mu, const float* sigma, T* out) {
+    for (int s = blockIdx.y; s < n_spectra; s += gridDim.y) {
+        const int64_t off = offsets ? offsets[s] : 0;
+        const int64_t N = offsets ? offsets[s + 1] - off : n_bins;
+        const float m = mu[s], sd = sigma[s];
+        const int64_t step = (int64_t)gridDim.x * blockDim.x;
+        const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        // elements before the first 16-byte boundary of the input, and after the last
+        const int64_t head = ((4 - (off & 3)) & 3) < N ? ((4 - (off & 3)) & 3) : N;
+        const int64_t nvec = (N - head) / 4;
+        if (t0 < head) out[off + t0] = narrow<T>(__fdiv_rn(__fsub_rn(p[off + t0], m), sd));
+        const float4* pv = reinterpret_cast<const float4*>(p + off + head);
+        uint2* ov = reinterpret_cast<uint2*>(out + off + head);
+        for (int64_t k = t0; k < nvec; k += step) {
+            const float4 v = __ldg(pv + k);
+            ov[k] = Pack4<T>::make(__fdiv_rn(__fsub_rn(v.x, m), sd), __fdiv_rn(__fsub_rn(v.y, m), sd),
+                                   __fdiv_rn(__fsub_rn(v.z, m), sd), __fdiv_rn(__fsub_rn(v.w, m), sd));
+        }
+        for (int64_t k = head + 4 * nvec + t0; k < N; k += step)
+            out[off + k] = narrow<T>(__fdiv_rn(__fsub_rn(p[off + k], m), sd));
+    }
 }
 
 cudaError_t launch_standardize_cast(const float* p, const int64_t* offsets, int n_spectra, int64_t n_bins,
                                     const float* mu, const float* sigma, hs_dtype dt, void* out, cudaStream_t s) {
-    unsigned gx = (unsigned)std::min<int64_t>((n_bins + 255) / 256, 4096);
-    if (gx == 0 || n_spectra == 0) return cudaSuccess;
-    dim3 grid(gx, (unsigned)n_spectra);
+    if (n_spectra == 0 || n_bins == 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // about eight resident blocks per SM in total, spread over spectra
+    const int64_t cap = std::max<int64_t>(64, (int64_t)sms * 8 / n_spectra);
+    const int64_t per_spec = std::max<int64_t>(1, std::min<int64_t>((n_bins / 4 + 255) / 256, cap));
+    const int64_t ys = std::max<int64_t>(1, std::min<int64_t>(n_spectra, (int64_t)sms * 8 / per_spec + 1));
+    dim3 grid((unsigned)per_spec, (unsigned)std::min<int64_t>(ys, 65535));
     if (dt == HS_F16)
-        k_standardize_cast<__half><<<grid, 256, 0, s>>>(p, offsets, n_bins, mu, sigma, (__half*)out);
+        k_standardize_cast<__half><<<grid, 256, 0, s>>>(p, offsets, n_spectra, n_bins, mu, sigma, (__half*)out);
     else
-        k_standardize_cast<__nv_bfloat16><<<grid, 256, 0, s>>>(p, offsets, n_bins, mu, sigma, (__nv_bfloat16*)out);
+        k_standardize_cast<__nv_bfloat16>
+            <<<grid, 256, 0, s>>>(p, offsets, n_spectra, n_bins, mu, sigma, (__nv_bfloat16*)out);
     return cudaGetLastError();
 }
 
