@@ -94,6 +94,20 @@ def test_constant_spectrum(variant, c):
         assert not r["path"].any()  # ties keep the left bin
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_calibration_closed_form(variant):
+    """A constant spectrum c has sum c*H, so the calibrated value is (c*sqrt(H) - mu_H) * isig_H for
+    any per-H tables: pins both the order (subtract, then scale) and the per-H indexing."""
+    N, hmax, c = 200, 32, 1.25
+    rng = np.random.default_rng(4)
+    mu = np.concatenate([[0.0], rng.uniform(-2, 2, hmax)])
+    isig = np.concatenate([[1.0], rng.uniform(0.2, 3, hmax)])
+    r = oracle.hs_1d(variant, np.full(N, c), hmax=hmax, mu=mu, isig=isig, fp64=True, all_h=True)
+    for n in range(0, N, 7):
+        for H in range(1, oracle.hvalid(variant, n, N, hmax) + 1):
+            assert r["all_h"][H - 1, n] == pytest.approx((c * math.sqrt(H) - mu[H]) * isig[H], rel=1e-13)
+
+
 def test_zero_spectrum_tie_break():
     x = np.zeros(100, np.float32)
     for v in VARIANTS:
@@ -383,6 +397,22 @@ def test_adjoint_is_transpose_of_linear_map(variant):
         hv = oracle.hs_1d(variant, v, hmax=hmax, fp64=True, all_h=True)["all_h"]
         lin = sum(g[n] * hv[bh[n] - 1, n] for n in range(N) if bh[n] > 0)
         assert float(grad @ v) == pytest.approx(lin, rel=1e-10)
+
+
+def test_adjoint_max_ties_route_to_first_maximum():
+    """On an integer spectrum full of ties, the Max adjoint sends each term's weight to the first
+    maximum of its window, the element numpy's argmax picks (brute force over every (n, i))."""
+    N, hmax = 400, 32
+    x = np.random.default_rng(8).integers(0, 3, N).astype(np.float64)
+    r = oracle.hs_1d("max", x, hmax=hmax, fp64=True)
+    g = np.random.default_rng(9).standard_normal(N)
+    grad = oracle.grad_1d("max", x, g, r["best_h"], hmax=hmax)
+    expect = np.zeros(N)
+    for n in range(N):
+        Hs = int(r["best_h"][n])
+        for i in range(1, Hs + 1):
+            expect[i * n + 1 + int(np.argmax(x[i * n + 1:i * n + i + 1]))] += g[n] / math.sqrt(Hs)
+    np.testing.assert_allclose(grad, expect, rtol=1e-12, atol=1e-12)
 
 
 def _routing(variant, x, hmax):
