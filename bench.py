@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default (or --tiles) tile sizes")
     ap.add_argument("--tiles", default="", help="variant=bins,... tile sizes to use instead of tuning")
     ap.add_argument("--cpu-sample-spectra", type=int, default=16)
+    ap.add_argument("--staged-spans", action="store_true",
+                    help="Eq. 1 with its input spans staged in shared memory by bulk copies (HS_FLAG_STAGED_SPANS)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the FP16/BF16, adjoint and 2-D measurements reported beside the main line")
     return ap.parse_args()
@@ -207,14 +209,14 @@ def run_reference(args):
 
 
 def csrc_sha16():
-    """Hash of the library sources, to tell whether a stored ncu traffic figure is still current."""
-    import glob
+    """Hash of the sources the batched 1-D kernels are built from, to tell whether a stored ncu
+    traffic figure still belongs to the kernel being timed."""
     import hashlib
 
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1812_02647_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(d, "*.cu")) + glob.glob(os.path.join(d, "*.cuh"))):
-        h.update(open(f, "rb").read())
+    for f in ("hs_1d.cu", "hs_common.cuh", "hs_farey.cuh", "hs_internal.cuh"):
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -223,7 +225,8 @@ def workload_config(args, offsets, variants):
                         "H_max=32, variants %s, persistent graph-captured launch per variant" %
                         (args.spectra, "+".join(variants)),
             "n_spectra": args.spectra, "total_bins": int(offsets[-1]), "hmax": HMAX, "variants": list(variants),
-            "threshold": THR, "l2": "inputs (%.1f GB) larger than L2; no flush" % (offsets[-1] * 4 / 1e9)}
+            "threshold": THR, "l2": "inputs (%.1f GB) larger than L2; no flush" % (offsets[-1] * 4 / 1e9),
+            "eq1_kernel": "staged spans" if args.staged_spans else "gather"}
 
 
 def _noise(torch, shape, seed, dtype=None):
@@ -363,7 +366,7 @@ def main():
         od = torch.from_numpy(offsets).cuda()
         cap = 1 << 24
         h = hs.HarmonicSum(variants=0xF, hmax=HMAX, max_bins=1 << 22, threshold=THR, cand_capacity=cap,
-                           max_spectra=args.spectra)
+                           max_spectra=args.spectra, flags=hs.FLAG_STAGED_SPANS if args.staged_spans else 0)
         for v in variants:
             mu, isig = hs.hs_noise_calibration(v, HMAX)
             h.set_calibration(v, mu, isig)
@@ -465,6 +468,30 @@ def main():
                    "api": "hs_sum_batched_host (8 pieces, copies overlapped with compute)",
                    "h2d_alone_ms": h2d_ms, "h2d_gbs": total * 4 / (h2d_ms / 1e3) / 1e9}
 
+        # Eq. 1 with the input spans staged in shared memory by bulk copies (plan flag), on the same
+        # batch after the timed region: its time next to the default gather path, and whether the
+        # results agree bit for bit
+        staged = None
+        if "std" in variants and not args.no_secondary and not args.staged_spans:
+            hst = hs.HarmonicSum(variants=hs.STD, hmax=HMAX, max_bins=1 << 22, threshold=THR, cand_capacity=cap,
+                                 max_spectra=args.spectra, flags=hs.FLAG_STAGED_SPANS)
+            mu, isig = hs.hs_noise_calibration("std", HMAX)
+            hst.set_calibration("std", mu, isig)
+            hs.hs_plan_set_tile_bins(hst.plan, "std", tuned["std"])
+            ost = hst.new_outputs(total, "std", "cuda")
+
+            def run_staged():
+                ost["cand_count"].zero_()
+                hs.hs_sum_batched(hst.plan, "std", xd, od, hst.out_struct(ost), hst.ws, 0, stream)
+
+            st_ms = _time_ms(torch, stream, run_staged, 2)
+            same = bool(torch.equal(ost["best_snr"], outs["std"]["best_snr"]) and
+                        torch.equal(ost["best_h"], outs["std"]["best_h"]))
+            staged = {"kernel": "hs::k_hs1d_eq1_staged (HS_FLAG_STAGED_SPANS)", "ms": st_ms,
+                      "default_gather_ms": statistics.mean(per_variant["std"]), "bit_identical_to_default": same}
+            del hst, ost
+            torch.cuda.empty_cache()
+
     value = world * total * HMAX / (step_ms / 1e3)
     peaks, peak_src = load_peaks()
     avg = {v: statistics.mean(per_variant[v]) for v in variants}
@@ -485,14 +512,15 @@ def main():
     traffic = None
     try:
         tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        if tj.get("csrc_sha16") == csrc_sha16() and dom == "std":
+        if tj.get("csrc_sha16") == csrc_sha16() and dom == "std" and not args.staged_spans:
             traffic = tj["dram_bytes_per_bin"] * total
     except Exception:
         pass
     if dom == "std":
         # Eq. 1 performs 528 ordered FP32 adds per bin (sum_{H<=32} H); its HBM bytes are negligible
         tf = 528.0 * total / (avg[dom] / 1e3) / 1e12
-        roof = {"bound": "alu", "kernel": "hs::k_hs1d_batched<Eq. 1>", "achieved": tf, "peak": alu_peak,
+        kname = "hs::k_hs1d_eq1_staged" if args.staged_spans else "hs::k_hs1d_batched<Eq. 1>"
+        roof = {"bound": "alu", "kernel": kname, "achieved": tf, "peak": alu_peak,
                 "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock", "unit": "TFLOP/s",
                 "frac": tf / alu_peak, "traffic": traffic, "algorithmic_flops_per_launch": 528.0 * total}
     else:
@@ -515,6 +543,8 @@ def main():
     }
     if e2e:
         line["e2e"] = e2e
+    if staged:
+        line["eq1_staged_spans"] = staged
     if not args.no_secondary:
         del graphs, outs, xd
         torch.cuda.empty_cache()

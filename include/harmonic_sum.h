@@ -65,6 +65,11 @@ typedef enum hs_dtype { HS_F32 = 0, HS_F16 = 1, HS_BF16 = 2 } hs_dtype;
 
 /* plan flags */
 #define HS_FLAG_OUT_ALL_H 1 /* hs_sum_1d may write the snr of every H (debug table) */
+/* Eq. 1 over a batch (hs_sum_batched, hmax 32, no every-H table): stage each Farey fraction's input
+ * span of a tile in shared memory with bulk copies and read it from there, the span-per-harmonic
+ * access pattern of Section 2 made explicit.  Results are bit-identical to the default path, which
+ * gathers through L1 and is faster on GB300; the flag exists for comparison. */
+#define HS_FLAG_STAGED_SPANS 2
 
 typedef struct hs_plan hs_plan; /* opaque; host memory only */
 

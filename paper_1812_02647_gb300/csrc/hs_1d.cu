@@ -4,6 +4,7 @@
 #include <utility>
 
 #include "hs_common.cuh"
+#include "hs_farey.cuh"
 
 namespace hs {
 
@@ -14,63 +15,6 @@ namespace hs {
 
 template <int V, typename T>
 struct Bin;
-
-// Eq. 1.  The index of harmonic i of H at output bin n, round-half-up(n*i/H), depends only on the
-// reduced fraction i/H, so each of the 324 distinct fractions of F_32 (the Farey sequence of order
-// 32) is read once and added to every S_H it belongs to.  Visiting the fractions in increasing
-// order adds the terms of each S_H in the order i = 1..H, as the definition does.
-struct Frac {
-    int p, q;
-};
-__host__ __device__ constexpr Frac farey_at(int k) {  // k-th term of F_32 after 0/1: 1/32, 1/31, ..., 1/1
-    Frac a{0, 1}, b{1, 32};
-    for (int i = 0; i < k; ++i) {
-        int m = (32 + a.q) / b.q;
-        Frac c{m * b.p - a.p, m * b.q - a.q};
-        a = b;
-        b = c;
-    }
-    return b;
-}
-constexpr int kNumFrac = 324;
-static_assert(farey_at(kNumFrac - 1).p == 1 && farey_at(kNumFrac - 1).q == 1, "F_32 has 324 terms after 0/1");
-
-// round-half-up(n*p/q) = floor((n*F + 2^31) / 2^32) with F = ceil(2^32 p/q): the error n*(F - 2^32 p/q)
-// / 2^32 < 2^-6 <= 1/(2q) for n < 2^26 never reaches the next multiple of 1/(2q), so this is exact.
-// It is evaluated in 32-bit pieces: high word of n*F plus the carry of (low word + 2^31).
-template <int P, int Q>
-struct FracConst {
-    static constexpr uint32_t F = (uint32_t)((((uint64_t)P << 32) + Q - 1) / Q);
-};
-
-template <int P, int Q>
-__device__ __forceinline__ uint32_t frac_index(uint32_t n) {
-    if (Q == 1) return n;
-    constexpr uint32_t F = FracConst<P, Q>::F;
-    return __umulhi(n, F) + ((n * F) >> 31);
-}
-
-template <typename T>
-__device__ __forceinline__ const T* elem_ptr(const T* x, uint32_t i) {
-    return x + i;
-}
-
-
-// Generic hmax: one output per call, harmonics beyond hmax skipped.
-template <typename T, int K>
-__device__ __forceinline__ void farey_step(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1]) {
-    constexpr Frac f = farey_at(K);
-    const float v = widen<T>(__ldg(elem_ptr(x, frac_index<f.p, f.q>(n))));
-#pragma unroll
-    for (int m = 1; m * f.q <= kHmax; ++m)
-        if (m * f.q <= hmax) S[m * f.q] = __fadd_rn(S[m * f.q], v);
-}
-
-template <typename T, int... K>
-__device__ __forceinline__ void farey_all(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1],
-                                          std::integer_sequence<int, K...>) {
-    (farey_step<T, K>(x, n, hmax, S), ...);  // in increasing fraction order
-}
 
 // hmax = 32, outputs n and n+1 together.  For fraction f <= 1 their bins differ by 0 or 1: with
 // W = n*F + 2^31, bin(n) = W >> 32 and bin(n+1) = (W + F) >> 32, which is one more exactly when
@@ -376,16 +320,6 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int64_t* offsets, int 
     }
 }
 
-// Last spectrum s with prefix[s] <= item (spectra with no tiles are skipped over).
-__device__ __forceinline__ int find_spectrum(const int64_t* prefix, int n_spectra, unsigned long long item) {
-    int lo = 0, hi = n_spectra - 1;
-    while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if ((unsigned long long)__ldg(prefix + mid) <= item) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // Persistent kernel: CTAs pop (spectrum, tile) items in order from the queue.  The next item is
 // claimed while the current one is processed, so the atomic's round trip is off the critical path.
 template <int V, typename T>
@@ -428,6 +362,11 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<V>::value) k_hs1d_batched(co
 // ------------------------------------------------------------------------------------------
 // host side
 // ------------------------------------------------------------------------------------------
+void launch_tile_scan(const int64_t* offsets, int n_spectra, int64_t tile, int64_t max_bins, int elem_bytes,
+                      int64_t* prefix, WsControl* ctl, cudaStream_t s) {
+    k_tile_scan<<<1, 1024, 0, s>>>(offsets, n_spectra, tile, max_bins, elem_bytes, prefix, ctl);
+}
+
 template <int V, typename T>
 static int& occupancy_slot() {
     static int occ = 0;  // resident CTAs per SM of the persistent kernel
@@ -454,7 +393,7 @@ static cudaError_t launch_typed(const Tables& tab, const Work1d& w, const Out1d&
         k_hs1d_single<V, T><<<grid, kBlock, 0, s>>>(tab, w, o, ctl);
         return cudaGetLastError();
     }
-    k_tile_scan<<<1, 1024, 0, s>>>(w.offsets, w.n_spectra, tile, w.max_bins, (int)sizeof(T), prefix, ctl);
+    launch_tile_scan(w.offsets, w.n_spectra, tile, w.max_bins, (int)sizeof(T), prefix, ctl, s);
     k_hs1d_batched<V, T><<<(unsigned)(sm_count * occupancy<V, T>()), kBlock, 0, s>>>(tab, w, o, ctl, prefix);
     return cudaGetLastError();
 }
@@ -479,7 +418,10 @@ static void warm_v(hs_dtype dt) {
 
 // Query occupancy outside any stream capture.
 void warm_1d(hs_variant v, hs_dtype dt) {
-    if (v == HS_STD) warm_v<HS_STD>(dt);
+    if (v == HS_STD) {
+        warm_v<HS_STD>(dt);
+        warm_eq1_staged(dt);
+    }
     if (v == HS_MAX) warm_v<HS_MAX>(dt);
     if (v == HS_FBIN) warm_v<HS_FBIN>(dt);
     if (v == HS_GREEDY) warm_v<HS_GREEDY>(dt);
@@ -487,6 +429,8 @@ void warm_1d(hs_variant v, hs_dtype dt) {
 
 cudaError_t launch_1d(hs_variant v, hs_dtype dt, const Tables& tab, const Work1d& w, const Out1d& o,
                       WsControl* ctl, int64_t* prefix, int sm_count, cudaStream_t s) {
+    if (v == HS_STD && (w.flags & HS_FLAG_STAGED_SPANS) && eq1_staged_applies(w, o))
+        return launch_eq1_staged(dt, tab, w, o, ctl, prefix, sm_count, s);
     switch (v) {
         case HS_STD: return launch_dtype<HS_STD>(dt, tab, w, o, ctl, prefix, sm_count, s);
         case HS_MAX: return launch_dtype<HS_MAX>(dt, tab, w, o, ctl, prefix, sm_count, s);

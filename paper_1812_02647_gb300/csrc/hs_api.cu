@@ -98,7 +98,7 @@ hs_status hs_plan_create(hs_plan** plan, const hs_plan_desc* d) {
     if (d->hmax < 1 || d->hmax > hcap) return HS_ERR_INVALID;
     if (d->max_bins < 0 || d->max_bins > HS_MAX_BINS_1D) return HS_ERR_INVALID;
     if (d->nz > 0 && (d->z_min > 0 || d->z_min + d->nz - 1 < 0 || d->nz > 32767)) return HS_ERR_INVALID;
-    if (d->cand_capacity < 0 || (d->flags & ~HS_FLAG_OUT_ALL_H) != 0) return HS_ERR_INVALID;
+    if (d->cand_capacity < 0 || (d->flags & ~(HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS)) != 0) return HS_ERR_INVALID;
     if (std::isnan(d->threshold)) return HS_ERR_INVALID;
     hs_plan* p = new (std::nothrow) hs_plan;
     if (!p) return HS_ERR_NOMEM;
@@ -212,6 +212,7 @@ hs_status hs_sum_1d(const hs_plan* p, hs_variant v, const void* d_x, int64_t n_b
     w.threshold = p->d.threshold;
     w.opt = p->launch[vindex(v)].opt;
     w.max_bins = p->d.max_bins;
+    w.flags = p->d.flags;
     WsControl* ctl = reinterpret_cast<WsControl*>(d_ws);
     int64_t* prefix = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(d_ws) + kWsControlBytes);
     return check_cuda(launch_1d(v, p->d.dtype, p->tab[vindex(v)], w, make_out(p, v, out), ctl, prefix,
@@ -238,6 +239,7 @@ hs_status hs_sum_batched(const hs_plan* p, hs_variant v, const void* d_x, const 
     w.threshold = p->d.threshold;
     w.opt = p->launch[vindex(v)].opt;
     w.max_bins = p->d.max_bins;
+    w.flags = p->d.flags;
     WsControl* ctl = reinterpret_cast<WsControl*>(d_ws);
     int64_t* prefix = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(d_ws) + kWsControlBytes);
     return check_cuda(launch_1d(v, p->d.dtype, p->tab[vindex(v)], w, make_out(p, v, out), ctl, prefix,

@@ -84,4 +84,14 @@ __device__ __forceinline__ void append_candidate(bool hit, hs_candidate* cand, u
     }
 }
 
+// Last spectrum s with prefix[s] <= item (spectra with no tiles are skipped over).
+__device__ __forceinline__ int find_spectrum(const int64_t* prefix, int n_spectra, unsigned long long item) {
+    int lo = 0, hi = n_spectra - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if ((unsigned long long)__ldg(prefix + mid) <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
 }  // namespace hs

@@ -1,0 +1,62 @@
+// The Farey sequence of order 32 and the exact fixed-point form of the Eq. 1 index, shared by the
+// 1-D kernels.
+#pragma once
+
+#include <utility>
+
+#include "hs_common.cuh"
+
+namespace hs {
+
+// Eq. 1.  The index of harmonic i of H at output bin n, round-half-up(n*i/H), depends only on the
+// reduced fraction i/H, so each of the 324 distinct fractions of F_32 (the Farey sequence of order
+// 32) is read once and added to every S_H it belongs to.  Visiting the fractions in increasing
+// order adds the terms of each S_H in the order i = 1..H, as the definition does.
+struct Frac {
+    int p, q;
+};
+__host__ __device__ constexpr Frac farey_at(int k) {  // k-th term of F_32 after 0/1: 1/32, 1/31, ..., 1/1
+    Frac a{0, 1}, b{1, 32};
+    for (int i = 0; i < k; ++i) {
+        int m = (32 + a.q) / b.q;
+        Frac c{m * b.p - a.p, m * b.q - a.q};
+        a = b;
+        b = c;
+    }
+    return b;
+}
+constexpr int kNumFrac = 324;
+static_assert(farey_at(kNumFrac - 1).p == 1 && farey_at(kNumFrac - 1).q == 1, "F_32 has 324 terms after 0/1");
+
+// round-half-up(n*p/q) = floor((n*F + 2^31) / 2^32) with F = ceil(2^32 p/q): the error n*(F - 2^32 p/q)
+// / 2^32 < 2^-6 <= 1/(2q) for n < 2^26 never reaches the next multiple of 1/(2q), so this is exact.
+// It is evaluated in 32-bit pieces: high word of n*F plus the carry of (low word + 2^31).
+template <int P, int Q>
+struct FracConst {
+    static constexpr uint32_t F = (uint32_t)((((uint64_t)P << 32) + Q - 1) / Q);
+};
+
+template <int P, int Q>
+__device__ __forceinline__ uint32_t frac_index(uint32_t n) {
+    if (Q == 1) return n;
+    constexpr uint32_t F = FracConst<P, Q>::F;
+    return __umulhi(n, F) + ((n * F) >> 31);
+}
+
+// Generic hmax: one output per call, harmonics beyond hmax skipped.
+template <typename T, int K>
+__device__ __forceinline__ void farey_step(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1]) {
+    constexpr Frac f = farey_at(K);
+    const float v = widen<T>(__ldg(x + frac_index<f.p, f.q>(n)));
+#pragma unroll
+    for (int m = 1; m * f.q <= kHmax; ++m)
+        if (m * f.q <= hmax) S[m * f.q] = __fadd_rn(S[m * f.q], v);
+}
+
+template <typename T, int... K>
+__device__ __forceinline__ void farey_all(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1],
+                                          std::integer_sequence<int, K...>) {
+    (farey_step<T, K>(x, n, hmax, S), ...);  // in increasing fraction order
+}
+
+}  // namespace hs

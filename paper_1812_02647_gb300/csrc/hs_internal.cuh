@@ -58,6 +58,7 @@ struct Work1d {
     float threshold;
     int opt;        // outputs per thread; a tile is kBlock * opt output bins
     int64_t max_bins;
+    int flags;      // plan flags (HS_FLAG_*)
 };
 
 struct Launch {
@@ -90,6 +91,17 @@ cudaError_t launch_1d(hs_variant v, hs_dtype dt, const Tables& tab, const Work1d
                       WsControl* ctl, int64_t* tile_prefix, int sm_count, cudaStream_t s);
 
 void warm_1d(hs_variant v, hs_dtype dt);
+
+// tile prefix sums of a batch and reset of its work queue (hs_1d.cu)
+void launch_tile_scan(const int64_t* offsets, int n_spectra, int64_t tile, int64_t max_bins, int elem_bytes,
+                      int64_t* prefix, WsControl* ctl, cudaStream_t s);
+
+// Eq. 1 over a batch with the input spans staged in shared memory (hs_1d_staged.cu): taken under
+// HS_FLAG_STAGED_SPANS for hmax = 32 without the every-H table
+bool eq1_staged_applies(const Work1d& w, const Out1d& o);
+cudaError_t launch_eq1_staged(hs_dtype dt, const Tables& tab, const Work1d& w, const Out1d& o, WsControl* ctl,
+                              int64_t* prefix, int sm_count, cudaStream_t s);
+void warm_eq1_staged(hs_dtype dt);
 
 // 2-D (hs_2d.cu)
 struct Work2d {

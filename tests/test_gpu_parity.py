@@ -183,6 +183,50 @@ def test_batched_uneven_bit_exact(hs_lib, torch, variant):
     _check_candidates(hs_lib, o, r["best_snr"], r["best_h"], offsets, first_id=100)
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_batched_staged_spans_bit_exact(hs_lib, torch, dtype):
+    """Eq. 1 with the input spans staged in shared memory (HS_FLAG_STAGED_SPANS): tiles of 1024
+    bins, short spectra and ragged tails evaluated directly, several items per spectrum, candidates."""
+    lens = [0, 8, 1024, 1024 + 8, 1032 + 8, 4096, 100003 - 3, 8200, 0, 250000, 1 << 18, 16]
+    lens = [(l + 7) // 8 * 8 for l in lens]  # 16-byte aligned starts for every storage type
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    x32 = hs_synth.batch(93, offsets)
+    xd, xw = _widen(torch, x32, dtype)
+    code = {"f32": 0, "f16": 1, "bf16": 2}[dtype]
+    hs, mu, isig = _make(hs_lib, "std", True, dtype=code, flags=hs_lib.FLAG_STAGED_SPANS, max_spectra=len(lens))
+    for tile_bins in (1024, 8192):  # one or eight 1024-bin tiles per work item
+        hs_lib.hs_plan_set_tile_bins(hs.plan, "std", tile_bins)
+        o = hs.sum_batched("std", xd, torch.from_numpy(offsets).cuda(), first_id=7)
+        assert hs.sync_status() == hs_lib.OK
+        r = oracle.hs_batched("std", xw, offsets, mu=mu, isig=isig, nthreads=8)
+        np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+        np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+        _check_candidates(hs_lib, o, r["best_snr"], r["best_h"], offsets, first_id=7)
+
+
+def test_staged_spans_slice_and_graph(hs_lib, torch):
+    """The staged path on a batch slice with absolute offsets, captured in a graph and replayed."""
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(12, lengths=(1 << 15, 1 << 16, 1 << 17))
+    x = hs_synth.batch(seed, offsets, pulsars)
+    xd = torch.from_numpy(x).cuda()
+    hs = hs_lib.HarmonicSum(variants=hs_lib.STD, threshold=THR, cand_capacity=1 << 16, max_spectra=12,
+                            flags=hs_lib.FLAG_STAGED_SPANS)
+    sl = torch.from_numpy(offsets[4:10].copy()).cuda()  # spectra 4..8, absolute offsets
+    o = hs.new_outputs(x.size, "std", "cuda")
+    g = hs_lib.hs_graph_create_batched(hs.plan, hs_lib.STD, xd, sl, [hs.out_struct(o)], hs.ws)
+    r = oracle.hs_batched("std", x, offsets, nthreads=8)
+    a, b = int(offsets[4]), int(offsets[9])
+    for rep in range(2):
+        o["cand_count"].zero_()
+        hs_lib.hs_graph_launch(g)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(o["best_snr"].cpu().numpy()[a:b], r["best_snr"][a:b])
+        np.testing.assert_array_equal(o["best_h"].cpu().numpy()[a:b], r["best_h"][a:b])
+        assert int(o["cand_count"].item()) == int((r["best_snr"][a:b] > THR).sum())
+    hs_lib.hs_graph_destroy(g)
+
+
 def test_batched_bad_layout_is_reported(hs_lib, torch):
     offsets = np.array([0, 1000, 999, 3000], np.int64)  # a negative length
     x = torch.zeros(4000, device="cuda")
