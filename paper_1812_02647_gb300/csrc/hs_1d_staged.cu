@@ -17,6 +17,7 @@
 // i = 1..H and the results are bit-identical to the per-bin definition.
 #include <algorithm>
 
+#include "hs_async.cuh"
 #include "hs_farey.cuh"
 
 namespace hs {
@@ -34,7 +35,6 @@ constexpr int kStSlots = 8;                       // ring of shared-memory slots
 constexpr int kStSlotBytes = 24 * 1024;
 constexpr int kStCtas = 1;                        // resident CTAs per SM
 constexpr int kStDescs = 4;                       // tile descriptors in flight
-constexpr long long kStWaitCycles = 1ll << 31;    // about one second at the SM clock
 
 // Where each fraction's span lives: group g of consecutive fractions fills one slot; a fraction's
 // region holds up to cap elements, enough for any tile (derivation at region_cap).
@@ -122,48 +122,6 @@ constexpr uint32_t kStEnd = 2u;     // no more work
 
 constexpr size_t kStSmemBytes = (size_t)kStSlots * kStSlotBytes + 2 * kStSlots * sizeof(uint64_t) +
                                 kStDescs * sizeof(StDesc) + 16;
-
-// ---- mbarrier and bulk-copy primitives ----
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return done != 0u;
-}
-// Waits for the phase of the given parity to complete; gives up after about a second, or as soon as
-// another role has raised the abort flag.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, const volatile int* abort_flag) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (abort_flag != nullptr && *abort_flag) return false;
-        if (clock64() - t0 > kStWaitCycles) return false;
-    }
-}
-__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
 
 struct StShared {
     unsigned char* slots;
@@ -462,8 +420,8 @@ __global__ void __launch_bounds__(kStThreads, kStCtas)
             mbar_init(sh.empty0 + 8 * k, (uint32_t)kStConsWarps);
         }
         *sh.abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        fence_mbarrier_init();
+        fence_proxy_async_shared();
     }
     __syncthreads();
     if (threadIdx.x >= kStCons)
