@@ -70,6 +70,11 @@ typedef enum hs_dtype { HS_F32 = 0, HS_F16 = 1, HS_BF16 = 2 } hs_dtype;
  * access pattern of Section 2 made explicit.  Results are bit-identical to the default path, which
  * gathers through L1 and is faster on GB300; the flag exists for comparison. */
 #define HS_FLAG_STAGED_SPANS 2
+/* Eq. 2 with the window j = 0..i: harmonic i adds the largest of x(i n) .. x(i n + i) (i + 1 bins)
+ * instead of x(i n + 1) .. x(i n + i) as written in Section 2, so that a pulsar between two bins is
+ * seen by its lower neighbour too.  Applies to the forward sums and the adjoint; the valid H are
+ * unchanged (H (n + 1) <= N - 1).  Calibrate with hs_noise_calibration_flags. */
+#define HS_FLAG_MAX_WINDOW0 4
 
 typedef struct hs_plan hs_plan; /* opaque; host memory only */
 
@@ -138,6 +143,11 @@ hs_status hs_plan_set_calibration(hs_plan* plan, hs_variant v, const float* mu, 
  * (Hn = harmonic number); for Eq. 4 mu_H = sqrt(H)/2, sigma_H = sqrt(5/4).  Writes hmax+1 floats
  * to each host array (isig = 1/sigma), computed in double and rounded once. */
 hs_status hs_noise_calibration(hs_variant v, int hmax, float* mu, float* isig);
+
+/* The same for the sums a plan with these flags computes: with HS_FLAG_MAX_WINDOW0, Eq. 2 windows
+ * hold i + 1 bins, so Hn(i+1) and k <= i+1 replace Hn(i) and k <= i above.  flags = 0 gives
+ * hs_noise_calibration. */
+hs_status hs_noise_calibration_flags(hs_variant v, int hmax, int flags, float* mu, float* isig);
 
 /* Bytes of device workspace a call needs for up to n_spectra spectra (1 for hs_sum_1d / 2-D).
  * The workspace holds the status word, the work queue and tile prefix sums; it must be 256-byte

@@ -16,8 +16,10 @@ import subprocess
 
 import numpy as np
 
-STD, MAX, FBIN, GREEDY = 1, 2, 4, 8
-VARIANTS = {"std": STD, "max": MAX, "fbin": FBIN, "greedy": GREEDY}
+STD, MAX, FBIN, GREEDY, MAX0 = 1, 2, 4, 8, 16
+# "max0": Eq. 2 with the window j = 0..i (bins i*n .. i*n+i), a variant flag; "max" is the window as
+# written, j = 1..i
+VARIANTS = {"std": STD, "max": MAX, "fbin": FBIN, "greedy": GREEDY, "max0": MAX0}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = [os.path.join(_HERE, "hs_oracle.c"), os.path.join(_HERE, "hs_oracle_body.h")]

@@ -12,7 +12,7 @@
  * of valid harmonics at output bin n of an N-bin spectrum is the largest H <= hmax whose reads
  * all lie in [0, N):
  *     Eq. 1 (STD)            always hmax (every index is <= n)
- *     Eq. 2, 4 (MAX, GREEDY) H*(n+1) <= N-1   (the furthest read is H*n+H)
+ *     Eq. 2, 4 (MAX, MAX0, GREEDY) H*(n+1) <= N-1   (the furthest read is H*n+H)
  *     Eq. 3 (FBIN)           H*n <= N-1        (n = 0 reads x(0) for every H)
  * A bin with no valid H gets snr = -inf and H = 0.
  */
@@ -27,6 +27,7 @@
 #define HS_O_MAX 2
 #define HS_O_FBIN 4
 #define HS_O_GREEDY 8
+#define HS_O_MAX0 16 /* Eq. 2 with the window j = 0..i (a variant flag; the paper writes j = 1..i) */
 #define HS_O_HMAX 32
 
 int hs_oracle_hvalid(int variant, int64_t n, int64_t N, int hmax) {
@@ -87,10 +88,11 @@ void hs_oracle_grad_f64(int variant, const double* x, int64_t N, int hmax, const
                 m = hs_oracle_eq1_index(n, i, Hs);
             } else if (variant == HS_O_FBIN) {
                 m = (int64_t)i * n;
-            } else if (variant == HS_O_MAX) {
+            } else if (variant == HS_O_MAX || variant == HS_O_MAX0) {
                 int64_t base = (int64_t)i * n;
-                m = base + 1;
-                for (int jj = 2; jj <= i; ++jj)
+                int j0 = variant == HS_O_MAX0 ? 0 : 1;
+                m = base + j0;
+                for (int jj = j0 + 1; jj <= i; ++jj)
                     if (x[base + jj] > x[m]) m = base + jj;
             } else {
                 int64_t base = (int64_t)i * n + j;
@@ -151,6 +153,8 @@ void hs_oracle_standardize_cast(const float* p, int64_t n, float mu, float sigma
  *   STD, FBIN: h is a scaled sum of H independent unit-variance terms -> (0, 1).
  *   MAX: the max of i iid Exp(1) has mean sum_{k<=i} 1/k and variance sum_{k<=i} 1/k^2, so
  *        mu_H = sum_{i<=H} (Hn(i) - 1) / sqrt(H),  sigma_H^2 = sum_{i<=H} sum_{k<=i} k^-2 / H.
+ *   MAX0: windows of i + 1 bins: the same with Hn(i+1) and k <= i+1 (windows of one bin n are
+ *        disjoint for n >= H, since (i+1) n > i n + i).
  *   GREEDY: each step is the max of two fresh iid Exp(1) bins: mean 1/2, variance 5/4, so
  *        mu_H = sqrt(H)/2, sigma_H = sqrt(5/4).
  * mu[0], sigma[0] are set to (0, 1).
@@ -160,9 +164,14 @@ void hs_oracle_noise_moments(int variant, int hmax, double* mu, double* sigma) {
     sigma[0] = 1.0;
     double m_acc = 0.0, v_acc = 0.0, harm = 0.0, harm2 = 0.0;
     for (int H = 1; H <= hmax; ++H) {
-        if (variant == HS_O_MAX) {
-            harm += 1.0 / H;
-            harm2 += 1.0 / ((double)H * H);
+        if (variant == HS_O_MAX || variant == HS_O_MAX0) {
+            int w = variant == HS_O_MAX0 ? H + 1 : H; /* bins in harmonic H's window */
+            if (H == 1 && variant == HS_O_MAX0) {
+                harm = 1.0;
+                harm2 = 1.0;
+            }
+            harm += 1.0 / w;
+            harm2 += 1.0 / ((double)w * w);
             m_acc += harm - 1.0;
             v_acc += harm2;
             mu[H] = m_acc / sqrt((double)H);

@@ -6,6 +6,7 @@
  * Readings of the paper used here (Section 2 of arXiv:1812.02647):
  *   Eq. 1  index of harmonic i of H at output bin n is round-half-up(n*i/H) = (2*n*i + H) div (2*H).
  *   Eq. 2  the max runs over the literal window j = 1..i, i.e. bins i*n+1 .. i*n+i; first max wins.
+ *          Variant flag MAX0: the window j = 0..i, bins i*n .. i*n+i.
  *   Eq. 3  bins i*n.
  *   Eq. 4  start with S = 0, j = 0; harmonic i compares x(i*n+j) (left) with x(i*n+j+1) (right);
  *          the right bin is taken only when strictly larger, and then j grows by one.
@@ -33,11 +34,13 @@ static void FN(hs_bin_)(int variant, const REAL* x, int64_t N, int64_t n, int hm
             if (variant == HS_O_STD) {
                 /* Eq. 1: a fresh sum of H terms for every H */
                 for (int i = 1; i <= H; ++i) sum = sum + x[hs_oracle_eq1_index(n, i, H)];
-            } else if (variant == HS_O_MAX) {
-                /* Eq. 2: harmonic H contributes the largest of x(H*n+1) .. x(H*n+H) */
+            } else if (variant == HS_O_MAX || variant == HS_O_MAX0) {
+                /* Eq. 2: harmonic H contributes the largest of x(H*n+j0) .. x(H*n+H), with j0 = 1 as
+                 * written (the MAX0 variant flag starts the window at j0 = 0) */
                 int64_t base = (int64_t)H * n;
-                REAL m = x[base + 1];
-                for (int jj = 2; jj <= H; ++jj) {
+                int j0 = variant == HS_O_MAX0 ? 0 : 1;
+                REAL m = x[base + j0];
+                for (int jj = j0 + 1; jj <= H; ++jj) {
                     REAL v = x[base + jj];
                     m = (v > m) ? v : m;
                 }

@@ -22,6 +22,7 @@ VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
 F32, F16, BF16 = 0, 1, 2
 FLAG_OUT_ALL_H = 1
 FLAG_STAGED_SPANS = 2
+FLAG_MAX_WINDOW0 = 4
 HMAX_1D, HMAX_2D = 32, 16
 
 OK, ERR_INVALID, ERR_ALIGN, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, 1, 2, 3, 4, 5, 6
@@ -65,6 +66,7 @@ def _load():
         "hs_plan_destroy": ([_P], I),
         "hs_plan_set_calibration": ([_P, I, _P, _P], I),
         "hs_noise_calibration": ([I, I, _P, _P], I),
+        "hs_noise_calibration_flags": ([I, I, I, _P, _P], I),
         "hs_plan_workspace_size": ([_P, I, ctypes.POINTER(SZ)], I),
         "hs_workspace_init": ([_P, _P, SZ, _P], I),
         "hs_sum_1d": ([_P, I, _P, I64, U32, ctypes.POINTER(Out), _P, SZ, _P], I),
@@ -149,11 +151,15 @@ def hs_plan_set_calibration(plan, variant, mu=None, isig=None):
                                         None if isig is None else isig.ctypes.data), "hs_plan_set_calibration")
 
 
-def hs_noise_calibration(variant, hmax=32):
+def hs_noise_calibration(variant, hmax=32, flags=0):
     mu = np.empty(hmax + 1, np.float32)
     isig = np.empty(hmax + 1, np.float32)
-    _check(_lib.hs_noise_calibration(_variant(variant), hmax, mu.ctypes.data, isig.ctypes.data),
-           "hs_noise_calibration")
+    if flags:
+        _check(_lib.hs_noise_calibration_flags(_variant(variant), hmax, int(flags), mu.ctypes.data, isig.ctypes.data),
+               "hs_noise_calibration_flags")
+    else:
+        _check(_lib.hs_noise_calibration(_variant(variant), hmax, mu.ctypes.data, isig.ctypes.data),
+               "hs_noise_calibration")
     return mu, isig
 
 

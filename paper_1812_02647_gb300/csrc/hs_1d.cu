@@ -50,7 +50,7 @@ template <typename T>
 struct Bin<HS_STD, T> {
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
-                                                uint32_t& path) {
+                                                uint32_t& path, uint32_t j0) {
         float S[kHmax + 1];
 #pragma unroll
         for (int H = 0; H <= kHmax; ++H) S[H] = 0.f;
@@ -118,17 +118,18 @@ __device__ __forceinline__ float window_max(const T* x, uint32_t N, uint32_t w0,
     return m;
 }
 
-// Eq. 2: harmonic i adds the largest of x(i*n+1) .. x(i*n+i).
+// Eq. 2: harmonic i adds the largest of x(i*n+j0) .. x(i*n+i), j0 = 1 as written (0 under
+// HS_FLAG_MAX_WINDOW0).
 template <typename T>
 struct Bin<HS_MAX, T> {
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
-                                                uint32_t& path) {
+                                                uint32_t& path, uint32_t j0) {
         const int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
         float S = 0.f;
         for (int i = 1; i <= hv; ++i) {
             const uint32_t base = (uint32_t)i * n;
-            S = __fadd_rn(S, window_max(x, N, base + 1, base + (uint32_t)i));
+            S = __fadd_rn(S, window_max(x, N, base + j0, base + (uint32_t)i));
             const float snr = calibrate(tb, S, i);
             keep_best(snr, i, best, bh);
             if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
@@ -143,7 +144,7 @@ template <typename T>
 struct Bin<HS_FBIN, T> {
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
-                                                uint32_t& path) {
+                                                uint32_t& path, uint32_t j0) {
         const int hv = (n == 0) ? hmax : (int)min((uint32_t)hmax, (N - 1) / n);
         float S = 0.f;
         for (int i0 = 1; i0 <= hv; i0 += 4) {
@@ -171,7 +172,7 @@ template <typename T>
 struct Bin<HS_GREEDY, T> {
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
-                                                uint32_t& path) {
+                                                uint32_t& path, uint32_t j0) {
         const int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
         float S = 0.f;
         uint32_t j = 0, p = 0;
@@ -225,7 +226,8 @@ __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, ui
         int bh = 0;
         uint32_t path = 0;
         if (active) {
-            Bin<V, T>::eval(x, N, n, w.hmax, tb, o.all_h, N, best, bh, path);
+            Bin<V, T>::eval(x, N, n, w.hmax, tb, o.all_h, N, best, bh, path,
+                            (w.flags & HS_FLAG_MAX_WINDOW0) ? 0u : 1u);
             o.best_snr[out_off + n] = best;
             o.best_h[out_off + n] = (uint8_t)bh;
             if (V == HS_GREEDY && o.path) o.path[out_off + n] = path;

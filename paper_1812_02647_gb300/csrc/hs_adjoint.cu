@@ -1,6 +1,7 @@
 // Adjoint of the per-bin best snr: a scatter-add transpose of the forward gather, routed through
 // the saved best H of every bin (and, for Eq. 4, the saved left/right choices; for Eq. 2 the
-// window's first maximum, recomputed from the spectrum).
+// window's first maximum, recomputed from the spectrum; the window starts at j0 = 1 as written, or
+// at j0 = 0 under HS_FLAG_MAX_WINDOW0).
 //   grad_x[m] += g[n] * c_H* * isig_H*   for every term of S_H*(n) that reads bin m.
 #include "hs_common.cuh"
 
@@ -10,8 +11,9 @@ constexpr int kAdjBlock = 256;
 
 template <int V, typename T>
 __global__ void __launch_bounds__(kAdjBlock) k_backward(const __grid_constant__ Tables tb, const T* x,
-                                                        const int64_t* offsets, int64_t n_bins, int hmax, const float* g,
-                                                        const uint8_t* best_h, const uint32_t* path, float* grad) {
+                                                        const int64_t* offsets, int64_t n_bins, int hmax, uint32_t j0,
+                                                        const float* g, const uint8_t* best_h, const uint32_t* path,
+                                                        float* grad) {
     const int s = blockIdx.y;
     const int64_t off = offsets ? offsets[s] : 0;
     const uint32_t N = (uint32_t)(offsets ? offsets[s + 1] - off : n_bins);
@@ -36,9 +38,9 @@ __global__ void __launch_bounds__(kAdjBlock) k_backward(const __grid_constant__ 
                 m = (uint32_t)i * n;
             } else if (V == HS_MAX) {
                 uint32_t base = (uint32_t)i * n;
-                m = base + 1;
+                m = base + j0;
                 float mv = ldx(xs, m);
-                for (int jj = 2; jj <= i; ++jj) {
+                for (int jj = (int)j0 + 1; jj <= i; ++jj) {
                     float v = ldx(xs, base + jj);
                     if (v > mv) {
                         mv = v;
@@ -56,35 +58,36 @@ __global__ void __launch_bounds__(kAdjBlock) k_backward(const __grid_constant__ 
 
 template <int V>
 static cudaError_t launch_v(hs_dtype dt, const Tables& tab, const void* x, const int64_t* offsets, int n_spectra,
-                            int64_t n_bins, int hmax, const float* g, const uint8_t* bh, const uint32_t* path, float* grad,
-                            cudaStream_t s) {
+                            int64_t n_bins, int hmax, uint32_t j0, const float* g, const uint8_t* bh, const uint32_t* path,
+                            float* grad, cudaStream_t s) {
     unsigned gx = (unsigned)std::min<int64_t>((n_bins + kAdjBlock - 1) / kAdjBlock, 2048);
     if (gx == 0) return cudaSuccess;
     dim3 grid(gx, (unsigned)n_spectra);
     switch (dt) {
         case HS_F32:
-            k_backward<V, float><<<grid, kAdjBlock, 0, s>>>(tab, (const float*)x, offsets, n_bins, hmax, g, bh, path, grad);
+            k_backward<V, float><<<grid, kAdjBlock, 0, s>>>(tab, (const float*)x, offsets, n_bins, hmax, j0, g, bh, path, grad);
             break;
         case HS_F16:
-            k_backward<V, __half><<<grid, kAdjBlock, 0, s>>>(tab, (const __half*)x, offsets, n_bins, hmax, g, bh, path, grad);
+            k_backward<V, __half><<<grid, kAdjBlock, 0, s>>>(tab, (const __half*)x, offsets, n_bins, hmax, j0, g, bh, path, grad);
             break;
         case HS_BF16:
             k_backward<V, __nv_bfloat16>
-                <<<grid, kAdjBlock, 0, s>>>(tab, (const __nv_bfloat16*)x, offsets, n_bins, hmax, g, bh, path, grad);
+                <<<grid, kAdjBlock, 0, s>>>(tab, (const __nv_bfloat16*)x, offsets, n_bins, hmax, j0, g, bh, path, grad);
             break;
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_backward(hs_variant v, hs_dtype dt, const Tables& tab, const void* x, const int64_t* offsets,
-                            int n_spectra, int64_t n_bins, int hmax, const float* g, const uint8_t* best_h,
+                            int n_spectra, int64_t n_bins, int hmax, int flags, const float* g, const uint8_t* best_h,
                             const uint32_t* path, float* grad, cudaStream_t s) {
+    const uint32_t j0 = (flags & HS_FLAG_MAX_WINDOW0) ? 0u : 1u;
     switch (v) {
-        case HS_STD: return launch_v<HS_STD>(dt, tab, x, offsets, n_spectra, n_bins, hmax, g, best_h, path, grad, s);
-        case HS_MAX: return launch_v<HS_MAX>(dt, tab, x, offsets, n_spectra, n_bins, hmax, g, best_h, path, grad, s);
-        case HS_FBIN: return launch_v<HS_FBIN>(dt, tab, x, offsets, n_spectra, n_bins, hmax, g, best_h, path, grad, s);
+        case HS_STD: return launch_v<HS_STD>(dt, tab, x, offsets, n_spectra, n_bins, hmax, j0, g, best_h, path, grad, s);
+        case HS_MAX: return launch_v<HS_MAX>(dt, tab, x, offsets, n_spectra, n_bins, hmax, j0, g, best_h, path, grad, s);
+        case HS_FBIN: return launch_v<HS_FBIN>(dt, tab, x, offsets, n_spectra, n_bins, hmax, j0, g, best_h, path, grad, s);
         case HS_GREEDY:
-            return launch_v<HS_GREEDY>(dt, tab, x, offsets, n_spectra, n_bins, hmax, g, best_h, path, grad, s);
+            return launch_v<HS_GREEDY>(dt, tab, x, offsets, n_spectra, n_bins, hmax, j0, g, best_h, path, grad, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -98,7 +98,7 @@ hs_status hs_plan_create(hs_plan** plan, const hs_plan_desc* d) {
     if (d->hmax < 1 || d->hmax > hcap) return HS_ERR_INVALID;
     if (d->max_bins < 0 || d->max_bins > HS_MAX_BINS_1D) return HS_ERR_INVALID;
     if (d->nz > 0 && (d->z_min > 0 || d->z_min + d->nz - 1 < 0 || d->nz > 32767)) return HS_ERR_INVALID;
-    if (d->cand_capacity < 0 || (d->flags & ~(HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS)) != 0) return HS_ERR_INVALID;
+    if (d->cand_capacity < 0 || (d->flags & ~(HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS | HS_FLAG_MAX_WINDOW0)) != 0) return HS_ERR_INVALID;
     if (std::isnan(d->threshold)) return HS_ERR_INVALID;
     hs_plan* p = new (std::nothrow) hs_plan;
     if (!p) return HS_ERR_NOMEM;
@@ -144,7 +144,13 @@ hs_status hs_plan_set_calibration(hs_plan* p, hs_variant v, const float* mu, con
 }
 
 hs_status hs_noise_calibration(hs_variant v, int hmax, float* mu, float* isig) {
+    return hs_noise_calibration_flags(v, hmax, 0, mu, isig);
+}
+
+hs_status hs_noise_calibration_flags(hs_variant v, int hmax, int flags, float* mu, float* isig) {
     if (!single_variant(v) || !mu || !isig || hmax < 1 || hmax > HS_HMAX_1D) return HS_ERR_INVALID;
+    if ((flags & ~(HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS | HS_FLAG_MAX_WINDOW0)) != 0) return HS_ERR_INVALID;
+    const int extra = (flags & HS_FLAG_MAX_WINDOW0) ? 1 : 0;  // Eq. 2 window of i + extra bins
     // standardised Exp(1) noise, bins far enough from 0 that every read is a distinct bin
     double hn = 0.0, hn2 = 0.0, mean_sum = 0.0, var_sum = 0.0;
     mu[0] = 0.f;
@@ -152,8 +158,14 @@ hs_status hs_noise_calibration(hs_variant v, int hmax, float* mu, float* isig) {
     for (int H = 1; H <= hmax; ++H) {
         double m = 0.0, sd = 1.0;
         if (v == HS_MAX) {
-            hn += 1.0 / H;                   // mean of the max of H unit exponentials
-            hn2 += 1.0 / ((double)H * H);    // and its variance
+            // mean and variance of the max of w = H + extra unit exponentials: Hn(w), sum_{k<=w} k^-2
+            if (H == 1 && extra) {
+                hn = 1.0;
+                hn2 = 1.0;
+            }
+            const double wn = H + extra;
+            hn += 1.0 / wn;
+            hn2 += 1.0 / (wn * wn);
             mean_sum += hn - 1.0;
             var_sum += hn2;
             m = mean_sum / std::sqrt((double)H);
@@ -285,7 +297,7 @@ hs_status hs_backward(const hs_plan* p, hs_variant v, const void* d_x, const int
     }
     if (n_spectra == 0) return HS_OK;
     return check_cuda(launch_backward(v, p->d.dtype, p->tab[vindex(v)], d_x, d_offsets, n_spectra, n_bins,
-                                      p->d.hmax, d_grad_snr, d_best_h, d_path, d_grad_x, stream));
+                                      p->d.hmax, p->d.flags, d_grad_snr, d_best_h, d_path, d_grad_x, stream));
 }
 
 hs_status hs_standardize_cast(const float* d_p, const int64_t* d_offsets, int n_spectra, int64_t n_bins,

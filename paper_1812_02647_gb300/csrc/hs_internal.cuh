@@ -116,7 +116,7 @@ cudaError_t launch_2d(const Tables& tab, const Work2d& w, const hs_out2d& o, lon
 
 // adjoint (hs_adjoint.cu)
 cudaError_t launch_backward(hs_variant v, hs_dtype dt, const Tables& tab, const void* x, const int64_t* offsets,
-                            int n_spectra, int64_t n_bins, int hmax, const float* g, const uint8_t* best_h,
+                            int n_spectra, int64_t n_bins, int hmax, int flags, const float* g, const uint8_t* best_h,
                             const uint32_t* path, float* grad, cudaStream_t s);
 
 // auxiliaries (hs_aux.cu)

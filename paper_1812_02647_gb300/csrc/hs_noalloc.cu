@@ -81,6 +81,7 @@ extern "C" hs_status hs_sum_batched_noalloc(const hs_plan* p, hs_variant v, cons
     w.threshold = p->d.threshold;
     w.opt = p->launch[vindex(v)].opt;
     w.max_bins = p->d.max_bins;
+    w.flags = p->d.flags;
     Out1d o;
     o.best_snr = out->best_snr;
     o.best_h = out->best_h;

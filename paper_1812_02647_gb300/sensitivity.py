@@ -24,7 +24,8 @@ T_SAMP = 64e-6  # s
 N_SAMPLES = int(round(T_OBS / T_SAMP))  # 312500
 DF = 1.0 / T_OBS  # bin width, Hz
 N_BINS = (N_SAMPLES // 2 + 1) // 8 * 8  # 156248: bins 0 .. N/2, trimmed to a 32-byte multiple
-VARIANTS = ("std", "max", "fbin", "greedy")
+# "max0" is Eq. 2 with the window j = 0..i (plan flag HS_FLAG_MAX_WINDOW0), beside the window as written
+VARIANTS = ("std", "max", "max0", "fbin", "greedy")
 
 
 def pulse_spectra(torch, f0_hz, amp=0.1, kappa=50.0, seed=0, device="cuda"):
@@ -54,7 +55,8 @@ def pulse_spectra(torch, f0_hz, amp=0.1, kappa=50.0, seed=0, device="cuda"):
 def pulsar_bins(variant, f_bins, hmax=32, n_bins=N_BINS):
     """Output bins where a variant reports a pulsar whose fundamental sits at ``f_bins`` (fractional
     bin).  Eq. 1 reports harmonic H's bin, n ~ H f (its output index is the H-th harmonic); Eq. 2-4
-    report the fundamental's bin (Eq. 2 reads x(n+1) .. for H = 1, so one bin lower is included)."""
+    report the fundamental's bin (Eq. 2 reads x(n+1) .. for H = 1, so one bin lower is included; the
+    same bins serve the j = 0..i window)."""
     if variant == "std":
         c = np.rint(np.arange(1, hmax + 1) * f_bins).astype(np.int64)
         cand = (c[:, None] + np.arange(-1, 2)[None, :]).ravel()
@@ -73,12 +75,17 @@ def _sum_all(hs_mod, torch, x, variants, hmax):
     b = x.shape[0]
     flat = x.reshape(-1)
     offsets = torch.arange(b + 1, device=x.device, dtype=torch.int64) * N_BINS
-    h = hs_mod.HarmonicSum(variants=0xF, hmax=hmax, max_bins=N_BINS, threshold=6.0, max_spectra=b)
+    plans = {}
     out = {}
     for v in variants:
-        mu, isig = hs_mod.hs_noise_calibration(v, hmax)
-        h.set_calibration(v, mu, isig)
-        o = h.sum_batched(v, flat, offsets)
+        flags = hs_mod.FLAG_MAX_WINDOW0 if v == "max0" else 0
+        if flags not in plans:
+            plans[flags] = hs_mod.HarmonicSum(variants=0xF, hmax=hmax, max_bins=N_BINS, threshold=6.0, max_spectra=b,
+                                              flags=flags)
+        h, lib_v = plans[flags], ("max" if v == "max0" else v)
+        mu, isig = hs_mod.hs_noise_calibration(lib_v, hmax, flags=flags)
+        h.set_calibration(lib_v, mu, isig)
+        o = h.sum_batched(lib_v, flat, offsets)
         out[v] = o["best_snr"].reshape(b, N_BINS).cpu().numpy()
     return out
 

@@ -95,6 +95,13 @@ def test_library_noise_calibration_matches_oracle(hs_lib):
         omu, oisig = oracle.noise_calibration(v, 32)
         np.testing.assert_array_equal(mu, omu)
         np.testing.assert_array_equal(isig, oisig)
+    # Eq. 2 with the window j = 0..i
+    mu, isig = hs_lib.hs_noise_calibration("max", 32, flags=hs_lib.FLAG_MAX_WINDOW0)
+    omu, oisig = oracle.noise_calibration("max0", 32)
+    np.testing.assert_array_equal(mu, omu)
+    np.testing.assert_array_equal(isig, oisig)
+    with pytest.raises(hs_lib.HSError):
+        hs_lib.hs_noise_calibration("max", 32, flags=64)
 
 
 def test_set_calibration_rejects_nonfinite(hs_lib):

@@ -390,6 +390,53 @@ def test_backward_matches_oracle_gradient(hs_lib, torch, variant):
     np.testing.assert_allclose(grad, exp, rtol=1e-5, atol=1e-6)
 
 
+# ---- Eq. 2 with the window j = 0..i (HS_FLAG_MAX_WINDOW0), against the oracle's "max0" ----
+
+def _max0(hs_lib, dtype=0, max_spectra=1, flags=0):
+    mu, isig = oracle.noise_calibration("max0", 32)
+    hs = hs_lib.HarmonicSum(variants=hs_lib.MAX, dtype=dtype, max_bins=1 << 22, threshold=THR, cand_capacity=1 << 16,
+                            flags=flags | hs_lib.FLAG_MAX_WINDOW0, max_spectra=max_spectra)
+    hs.set_calibration("max", mu, isig)
+    return hs, mu, isig
+
+
+@pytest.mark.parametrize("n_bins", [2, 3, 33, 1000, 65536 + 13, 300001])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_max_window0_bit_exact(hs_lib, torch, n_bins, dtype):
+    x = hs_synth.spectrum(77, 0, n_bins)
+    xd, xw = _widen(torch, x, dtype)
+    hs, mu, isig = _max0(hs_lib, dtype={"f32": 0, "f16": 1, "bf16": 2}[dtype], flags=hs_lib.FLAG_OUT_ALL_H)
+    o = hs.sum_1d("max", xd, all_h=True)
+    r = oracle.hs_1d("max0", xw, hmax=32, mu=mu, isig=isig, all_h=True, nthreads=8)
+    np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    _check_candidates(hs_lib, o, r["best_snr"], r["best_h"])
+
+
+def test_max_window0_batched_and_adjoint(hs_lib, torch):
+    lens = [0, 8, 4096, 100000, 12, 250000]
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    x = hs_synth.batch(95, offsets)
+    hs, mu, isig = _max0(hs_lib, max_spectra=len(lens))
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda()
+    o = hs.sum_batched("max", xd, od, first_id=3)
+    assert hs.sync_status() == hs_lib.OK
+    r = oracle.hs_batched("max0", x, offsets, mu=mu, isig=isig, nthreads=8)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    _check_candidates(hs_lib, o, r["best_snr"], r["best_h"], offsets, first_id=3)
+    g = torch.sigmoid(o["best_snr"] - 5.0)
+    grad = hs.backward("max", xd, g, o["best_h"], None, od).cpu().numpy().astype(np.float64)
+    gn = g.cpu().numpy().astype(np.float64)
+    exp = np.zeros(x.size)
+    for s in range(len(lens)):
+        a, b = offsets[s], offsets[s + 1]
+        exp[a:b] = oracle.grad_1d("max0", x[a:b], gn[a:b], r["best_h"][a:b], isig=isig.astype(np.float64))
+    np.testing.assert_allclose(grad, exp, rtol=1e-5, atol=1e-6)
+
+
 def test_autograd_function(hs_lib, torch):
     N = 1 << 14
     x = torch.from_numpy(hs_synth.spectrum(8, 0, N)).cuda().requires_grad_(True)

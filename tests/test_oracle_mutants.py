@@ -26,10 +26,14 @@ MUTANTS = [
      "for (int i = 1; i <= H; ++i) sum = sum + x[hs_oracle_eq1_index(n, i, H)];",
      "for (int i = 1; i < H; ++i) sum = sum + x[hs_oracle_eq1_index(n, i, H)];",
      ["test_h1_identity", "test_constant_spectrum"]),
-    ("max window shifted by one", "hs_oracle_body.h",
-     "REAL m = x[base + 1];\n                for (int jj = 2; jj <= H; ++jj) {\n                    REAL v = x[base + jj];",
-     "REAL m = x[base];\n                for (int jj = 1; jj < H; ++jj) {\n                    REAL v = x[base + jj];",
-     ["test_h1_identity", "test_delta_spike_max", "test_max_bruteforce"]),
+    ("max window starts at j = 0", "hs_oracle_body.h", "int j0 = variant == HS_O_MAX0 ? 0 : 1;",
+     "int j0 = variant == HS_O_MAX0 ? 0 : 0;", ["test_h1_identity", "test_max_bruteforce"]),
+    ("max0 window starts at j = 1", "hs_oracle_body.h", "int j0 = variant == HS_O_MAX0 ? 0 : 1;",
+     "int j0 = variant == HS_O_MAX0 ? 1 : 1;", ["test_h1_identity", "test_max_bruteforce"]),
+    ("max window ends one bin early", "hs_oracle_body.h", "for (int jj = j0 + 1; jj <= H; ++jj) {",
+     "for (int jj = j0 + 1; jj < H; ++jj) {", ["test_delta_spike_max", "test_max_bruteforce"]),
+    ("max0 noise moments with the max window", "hs_oracle.c", "int w = variant == HS_O_MAX0 ? H + 1 : H;",
+     "int w = H;", ["test_noise_calibration_tables"]),
     ("greedy takes the right bin on ties", "hs_oracle_body.h", "if (r > l) {", "if (r >= l) {",
      ["test_constant_spectrum", "test_greedy_bruteforce_paths"]),
     ("freq-bin reads the neighbour", "hs_oracle_body.h", "S = S + x[(int64_t)H * n];",
@@ -77,7 +81,9 @@ def _build_mutant(tmp, fname, old, new):
 
 def _run_pin(name):
     fn = getattr(pins, name)
-    params = {"test_h1_identity": [("std",), ("max",), ("fbin",), ("greedy",)],
+    params = {"test_h1_identity": [(v,) for v in pins.VARIANTS],
+              "test_max_bruteforce": [("max",), ("max0",)],
+              "test_delta_spike_max": [("max",), ("max0",)],
               "test_constant_spectrum": [(v, c) for v in pins.VARIANTS for c in (1.0, 3.5)],
               "test_range_limits": [(v,) for v in pins.VARIANTS],
               "test_linearity": [("std",), ("fbin",)],
@@ -116,7 +122,7 @@ def test_unmutated_copy_passes(tmp_path, monkeypatch):
             f, g = getattr(real, attr), getattr(mutant, attr)
             g.argtypes, g.restype = f.argtypes, f.restype
     monkeypatch.setattr(oracle, "_lib", mutant)
-    for pin in ("test_golden_1d_hand_worked", "test_delta_spike_eq1", "test_max_bruteforce",
+    for pin in ("test_golden_1d_hand_worked", "test_delta_spike_eq1", "test_max_bruteforce", "test_noise_calibration_tables",
                 "test_greedy_bruteforce_paths", "test_zero_spectrum_tie_break", "test_golden_2d_hand_worked",
                 "test_calibration_closed_form", "test_adjoint_max_ties_route_to_first_maximum"):
         _run_pin(pin)

@@ -16,7 +16,12 @@ import hs_synth
 import oracle
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-VARIANTS = ["std", "max", "fbin", "greedy"]
+VARIANTS = ["std", "max", "fbin", "greedy", "max0"]  # max0: Eq. 2 with the window j = 0..i (variant flag)
+
+
+def j0(variant):
+    """First window offset of Eq. 2: j = 1 as written, j = 0 under the variant flag."""
+    return 0 if variant == "max0" else 1
 
 
 def half_up(fr: Fraction) -> int:
@@ -68,6 +73,8 @@ def test_h1_identity(variant):
         expect = x
     elif variant == "max":
         expect = np.append(x[1:], -np.inf)  # x(n+1); the last bin has no valid H
+    elif variant == "max0":
+        expect = np.append(np.maximum(x[:-1], x[1:]), -np.inf)  # max(x(n), x(n+1))
     else:
         expect = np.append(np.maximum(x[:-1], x[1:]), -np.inf)
     np.testing.assert_array_equal(row, expect.astype(np.float32))
@@ -161,14 +168,15 @@ def test_delta_spike_fbin():
             assert r["all_h"][H - 1, n] == pytest.approx(A * hit / math.sqrt(H), abs=1e-15)
 
 
-def test_delta_spike_max():
+@pytest.mark.parametrize("variant", ["max", "max0"])
+def test_delta_spike_max(variant):
     N, hmax, m0, A = 300, 16, 95, 3.0
     x = np.zeros(N)
     x[m0] = A
-    r = oracle.hs_1d("max", x, hmax=hmax, fp64=True, all_h=True)
+    r = oracle.hs_1d(variant, x, hmax=hmax, fp64=True, all_h=True)
     for n in range(N):
-        for H in range(1, oracle.hvalid("max", n, N, hmax) + 1):
-            cnt = sum(1 for i in range(1, H + 1) if i * n + 1 <= m0 <= i * n + i)
+        for H in range(1, oracle.hvalid(variant, n, N, hmax) + 1):
+            cnt = sum(1 for i in range(1, H + 1) if i * n + j0(variant) <= m0 <= i * n + i)
             assert r["all_h"][H - 1, n] == pytest.approx(A * cnt / math.sqrt(H), abs=1e-15)
 
 
@@ -234,17 +242,18 @@ def test_2d_best_over_rows():
 # brute force on tiny spectra
 # ---------------------------------------------------------------------------------------------
 
-def test_max_bruteforce():
+@pytest.mark.parametrize("variant", ["max", "max0"])
+def test_max_bruteforce(variant):
     for seed in range(5):
         N = 64
         x = rand_spectrum(N, 500 + seed)
-        r32 = oracle.hs_1d("max", x, hmax=32, all_h=True)
-        r64 = oracle.hs_1d("max", x, hmax=32, fp64=True, all_h=True)
+        r32 = oracle.hs_1d(variant, x, hmax=32, all_h=True)
+        r64 = oracle.hs_1d(variant, x, hmax=32, fp64=True, all_h=True)
         for n in range(N):
             s32, s64 = np.float32(0), 0.0
-            for H in range(1, oracle.hvalid("max", n, N, 32) + 1):
-                win = x[H * n + 1: H * n + H + 1]
-                assert len(win) == H
+            for H in range(1, oracle.hvalid(variant, n, N, 32) + 1):
+                win = x[H * n + j0(variant): H * n + H + 1]
+                assert len(win) == H + 1 - j0(variant)
                 s32 = np.float32(s32 + win.max())
                 s64 += float(win.max())
                 assert r32["all_h"][H - 1, n] == np.float32(s32 * np.float32(1 / math.sqrt(H)))
@@ -329,6 +338,12 @@ def test_noise_calibration_tables():
     assert sd[2] == pytest.approx(math.sqrt(2.25 / 2), rel=1e-15)
     mu, sd = oracle.noise_moments("greedy", 32)
     assert mu[16] == pytest.approx(2.0) and sd[7] == pytest.approx(math.sqrt(1.25))
+    # windows of i + 1 bins: H = 1 is the max of two Exp(1) (mean 3/2, variance 5/4), H = 2 adds the
+    # max of three (mean 11/6, variance 1 + 1/4 + 1/9)
+    mu, sd = oracle.noise_moments("max0", 32)
+    assert mu[1] == pytest.approx(0.5, rel=1e-15) and sd[1] == pytest.approx(math.sqrt(1.25), rel=1e-15)
+    assert mu[2] == pytest.approx((0.5 + 5.0 / 6.0) / math.sqrt(2), rel=1e-15)
+    assert sd[2] == pytest.approx(math.sqrt((1.25 + 1.25 + 1.0 / 9.0) / 2), rel=1e-15)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -348,8 +363,8 @@ def _abs_term_sum(variant, x64, hmax, r64):
     j = np.zeros(N, np.int64)
     for H in range(1, hmax + 1):
         ok = H * (n + 1) <= N - 1
-        if variant == "max":
-            w = np.stack([x64[np.minimum(H * n + k, N - 1)] for k in range(1, H + 1)])
+        if variant in ("max", "max0"):
+            w = np.stack([x64[np.minimum(H * n + k, N - 1)] for k in range(j0(variant), H + 1)])
             t = np.abs(w.max(axis=0))
         else:
             bit = (r64["path"].astype(np.int64) >> (H - 1)) & 1
@@ -421,12 +436,12 @@ def _routing(variant, x, hmax):
     key = [r["best_h"].astype(np.int64)]
     if variant == "greedy":
         key.append(r["path"].astype(np.int64))
-    if variant == "max":
+    if variant in ("max", "max0"):
         N = x.shape[0]
         n = np.arange(N)
         for i in range(1, hmax + 1):
             ok = i * (n + 1) <= N - 1
-            w = np.stack([x[np.minimum(i * n + k, N - 1)] for k in range(1, i + 1)])
+            w = np.stack([x[np.minimum(i * n + k, N - 1)] for k in range(j0(variant), i + 1)])
             key.append(np.where(ok, np.argmax(w, axis=0), -1))
     return r, np.stack(key)
 
