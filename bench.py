@@ -492,6 +492,30 @@ def main():
             del hst, ost
             torch.cuda.empty_cache()
 
+        # the power-of-two stage search (H = 1, 2, 4, .., 32 only) on the same batch, after the timed
+        # region: per-variant times next to the every-H search above
+        pow2 = None
+        if not args.no_secondary and not args.staged_spans:
+            hp = hs.HarmonicSum(variants=0xF, hmax=HMAX, max_bins=1 << 22, threshold=THR, cand_capacity=cap,
+                                max_spectra=args.spectra, flags=hs.FLAG_POW2_STAGES)
+            op = hp.new_outputs(total, "greedy", "cuda")
+            per_p2 = {}
+            for v in variants:
+                mu, isig = hs.hs_noise_calibration(v, HMAX)
+                hp.set_calibration(v, mu, isig)
+                hs.hs_plan_set_tile_bins(hp.plan, v, tuned[v])
+
+                def run_p2(v=v):
+                    op["cand_count"].zero_()
+                    hs.hs_sum_batched(hp.plan, v, xd, od, hp.out_struct(op), hp.ws, 0, stream)
+
+                per_p2[v] = _time_ms(torch, stream, run_p2, 2)
+            pow2 = {"flag": "HS_FLAG_POW2_STAGES", "stages": [1, 2, 4, 8, 16, 32], "per_variant_ms": per_p2,
+                    "ms_per_step": sum(per_p2.values()),
+                    "speedup_vs_every_h": {v: statistics.mean(per_variant[v]) / per_p2[v] for v in variants}}
+            del hp, op
+            torch.cuda.empty_cache()
+
     value = world * total * HMAX / (step_ms / 1e3)
     peaks, peak_src = load_peaks()
     avg = {v: statistics.mean(per_variant[v]) for v in variants}
@@ -545,6 +569,8 @@ def main():
         line["e2e"] = e2e
     if staged:
         line["eq1_staged_spans"] = staged
+    if pow2:
+        line["pow2_stages"] = pow2
     if not args.no_secondary:
         del graphs, outs, xd
         torch.cuda.empty_cache()

@@ -75,6 +75,11 @@ typedef enum hs_dtype { HS_F32 = 0, HS_F16 = 1, HS_BF16 = 2 } hs_dtype;
  * seen by its lower neighbour too.  Applies to the forward sums and the adjoint; the valid H are
  * unchanged (H (n + 1) <= N - 1).  Calibrate with hs_noise_calibration_flags. */
 #define HS_FLAG_MAX_WINDOW0 4
+/* 1-D plans: search only the power-of-two stages H = 1, 2, 4, 8, 16, 32 (as SIGPROC and PRESTO do)
+ * instead of every H = 1..hmax.  Eq. 1 then reads only the 32 fractions i/32 and adds 63 terms per
+ * bin; Eq. 2-4 still add every harmonic to their running sums.  The every-H table reads -inf for
+ * H that are not stages. */
+#define HS_FLAG_POW2_STAGES 8
 
 typedef struct hs_plan hs_plan; /* opaque; host memory only */
 

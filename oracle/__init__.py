@@ -17,6 +17,7 @@ import subprocess
 import numpy as np
 
 STD, MAX, FBIN, GREEDY, MAX0 = 1, 2, 4, 8, 16
+POW2 = 64  # flag bit: search only H = 1, 2, 4, .. (pass pow2=True)
 # "max0": Eq. 2 with the window j = 0..i (bins i*n .. i*n+i), a variant flag; "max" is the window as
 # written, j = 1..i
 VARIANTS = {"std": STD, "max": MAX, "fbin": FBIN, "greedy": GREEDY, "max0": MAX0}
@@ -68,8 +69,8 @@ def _ptr(a):
     return None if a is None else a.ctypes.data
 
 
-def _variant(v):
-    return VARIANTS[v] if isinstance(v, str) else int(v)
+def _variant(v, pow2=False):
+    return (VARIANTS[v] if isinstance(v, str) else int(v)) | (POW2 if pow2 else 0)
 
 
 def _threads(n):
@@ -93,20 +94,20 @@ def _tables(mu, isig, hmax, dt):
     return mu, isig
 
 
-def hs_1d(variant, x, hmax: int = 32, mu=None, isig=None, fp64: bool = False, all_h: bool = False,
+def hs_1d(variant, x, hmax: int = 32, mu=None, isig=None, fp64: bool = False, pow2: bool = False, all_h: bool = False,
           nthreads: int | None = None):
     """Per-bin best snr / H (and the greedy path, and optionally every H's snr) of one spectrum.
 
     FP32 mode takes float32 input; FP64 mode widens the input to float64 and computes in double.
     """
-    v = _variant(variant)
+    v = _variant(variant, pow2)
     dt = np.float64 if fp64 else np.float32
     x = np.ascontiguousarray(x, dtype=dt)
     N = x.shape[0]
     mu, isig = _tables(mu, isig, hmax, dt)
     best = np.empty(N, dt)
     bh = np.empty(N, np.uint8)
-    path = np.zeros(N, np.uint32) if v == GREEDY else None
+    path = np.zeros(N, np.uint32) if v & ~POW2 == GREEDY else None
     ah = np.empty((hmax, N), dt) if all_h else None
     fn = _load().hs_oracle_1d_f64 if fp64 else _load().hs_oracle_1d_f32
     fn(v, _ptr(x), N, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh), _ptr(path), _ptr(ah), _threads(nthreads))
@@ -118,9 +119,9 @@ def hs_1d(variant, x, hmax: int = 32, mu=None, isig=None, fp64: bool = False, al
     return out
 
 
-def hs_bins(variant, x, bins, hmax: int = 32, mu=None, isig=None, fp64: bool = False):
+def hs_bins(variant, x, bins, hmax: int = 32, mu=None, isig=None, fp64: bool = False, pow2: bool = False):
     """Best snr / H / path of the listed output bins of one spectrum only."""
-    v = _variant(variant)
+    v = _variant(variant, pow2)
     dt = np.float64 if fp64 else np.float32
     x = np.ascontiguousarray(x, dtype=dt)
     bins = np.ascontiguousarray(bins, dtype=np.int64)
@@ -135,9 +136,9 @@ def hs_bins(variant, x, bins, hmax: int = 32, mu=None, isig=None, fp64: bool = F
     return {"best_snr": best, "best_h": bh, "path": path}
 
 
-def hs_batched(variant, x, offsets, hmax: int = 32, mu=None, isig=None, fp64: bool = False,
+def hs_batched(variant, x, offsets, hmax: int = 32, mu=None, isig=None, fp64: bool = False, pow2: bool = False,
                nthreads: int | None = None):
-    v = _variant(variant)
+    v = _variant(variant, pow2)
     dt = np.float64 if fp64 else np.float32
     x = np.ascontiguousarray(x, dtype=dt)
     offsets = np.ascontiguousarray(offsets, dtype=np.int64)
@@ -147,7 +148,7 @@ def hs_batched(variant, x, offsets, hmax: int = 32, mu=None, isig=None, fp64: bo
     mu, isig = _tables(mu, isig, hmax, dt)
     best = np.empty(total, dt)
     bh = np.empty(total, np.uint8)
-    path = np.zeros(total, np.uint32) if v == GREEDY else None
+    path = np.zeros(total, np.uint32) if v & ~POW2 == GREEDY else None
     fn = _load().hs_oracle_batched_f64 if fp64 else _load().hs_oracle_batched_f32
     fn(v, _ptr(x[base:base + total]), _ptr(offs), len(offs) - 1, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh),
        _ptr(path), _threads(nthreads))

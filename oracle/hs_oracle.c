@@ -28,9 +28,11 @@
 #define HS_O_FBIN 4
 #define HS_O_GREEDY 8
 #define HS_O_MAX0 16 /* Eq. 2 with the window j = 0..i (a variant flag; the paper writes j = 1..i) */
+#define HS_O_POW2 64 /* flag bit OR'ed into a variant: only H = 1, 2, 4, .. are stages of the search */
 #define HS_O_HMAX 32
 
 int hs_oracle_hvalid(int variant, int64_t n, int64_t N, int hmax) {
+    variant &= ~HS_O_POW2;
     if (variant == HS_O_STD) return hmax;
     int64_t lim;
     if (variant == HS_O_FBIN) {
@@ -76,6 +78,7 @@ static inline int64_t hs_oracle_floor_div(int64_t a, int64_t b) {
  */
 void hs_oracle_grad_f64(int variant, const double* x, int64_t N, int hmax, const double* isig_in,
                         const double* g, const uint8_t* best_h, double* grad_x) {
+    variant &= ~HS_O_POW2; /* the routing is the saved best H either way */
     for (int64_t n = 0; n < N; ++n) {
         int Hs = best_h[n];
         if (Hs <= 0 || Hs > hmax || g[n] == 0.0) continue;

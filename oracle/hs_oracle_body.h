@@ -12,6 +12,8 @@
  *          the right bin is taken only when strictly larger, and then j grows by one.
  *   Terms are summed in the order i = 1..H; h = S * c_H with c_H = 1/sqrt(H);
  *   snr = (h - mu_H) * isig_H; the best H is the first H with the largest snr.
+ *   Variant flag POW2 (the stages of SIGPROC/PRESTO-style searches): only H = 1, 2, 4, 8, .. are
+ *   searched; the other H report snr = -inf (Eq. 2-4 still add their terms to the running sum).
  */
 #define CAT2_(a, b) a##b
 #define CAT2(a, b) CAT2_(a, b)
@@ -21,6 +23,8 @@
 static void FN(hs_bin_)(int variant, const REAL* x, int64_t N, int64_t n, int hmax, const REAL* cs,
                         const REAL* mu, const REAL* isig, REAL* best_out, uint8_t* h_out,
                         uint32_t* path_out, REAL* all_h, int64_t all_h_stride) {
+    const int pow2 = (variant & HS_O_POW2) != 0; /* stages H = 1, 2, 4, ..: other H are not searched */
+    variant &= ~HS_O_POW2;
     int hv = hs_oracle_hvalid(variant, n, N, hmax);
     REAL best = -INFINITY;
     int best_h = 0;
@@ -29,7 +33,9 @@ static void FN(hs_bin_)(int variant, const REAL* x, int64_t N, int64_t n, int hm
     uint32_t path = 0; /* Eq. 4 choices: bit i-1 set when harmonic i took the right bin */
     for (int H = 1; H <= hmax; ++H) {
         REAL snr = -INFINITY;
-        if (H <= hv) {
+        const int stage = !pow2 || (H & (H - 1)) == 0;
+        /* Eq. 1 sums are independent per H, so its non-stage H are not computed at all */
+        if (H <= hv && (stage || variant != HS_O_STD)) {
             REAL sum = 0;
             if (variant == HS_O_STD) {
                 /* Eq. 1: a fresh sum of H terms for every H */
@@ -63,11 +69,13 @@ static void FN(hs_bin_)(int variant, const REAL* x, int64_t N, int64_t n, int hm
                 S = S + t;
                 sum = S;
             }
-            REAL h = sum * cs[H];
-            snr = (h - mu[H]) * isig[H];
-            if (snr > best) {
-                best = snr;
-                best_h = H;
+            if (stage) {
+                REAL h = sum * cs[H];
+                snr = (h - mu[H]) * isig[H];
+                if (snr > best) {
+                    best = snr;
+                    best_h = H;
+                }
             }
         }
         if (all_h) all_h[(int64_t)(H - 1) * all_h_stride + n] = snr;

@@ -19,9 +19,10 @@ struct Bin;
 // hmax = 32, outputs n and n+1 together.  For fraction f <= 1 their bins differ by 0 or 1: with
 // W = n*F + 2^31, bin(n) = W >> 32 and bin(n+1) = (W + F) >> 32, which is one more exactly when
 // the low word of W carries on adding F.  Both candidates are loaded and the carry picks one.
-template <typename T, int K>
+template <typename T, int K, bool P2>
 __device__ __forceinline__ void farey_pair_step(const T* x, uint32_t n, float2 (&S)[kHmax + 1]) {
     constexpr Frac f = farey_at(K);
+    if constexpr (P2 && !is_pow2(f.q)) return;  // not read by any power-of-two stage
     float2 v;
     if (f.q == 1) {
         const T* p = x + n;
@@ -37,27 +38,33 @@ __device__ __forceinline__ void farey_pair_step(const T* x, uint32_t n, float2 (
         v.y = (lo + 0x80000000u > 0xFFFFFFFFu - F) ? b : a;
     }
 #pragma unroll
-    for (int m = 1; m * f.q <= kHmax; ++m) S[m * f.q] = add2(S[m * f.q], v);
+    for (int m = 1; m * f.q <= kHmax; ++m)
+        if (!P2 || is_pow2(m)) S[m * f.q] = add2(S[m * f.q], v);
 }
 
-template <typename T, int... K>
+template <typename T, bool P2, int... K>
 __device__ __forceinline__ void farey_pair_all(const T* x, uint32_t n, float2 (&S)[kHmax + 1],
                                                std::integer_sequence<int, K...>) {
-    (farey_pair_step<T, K>(x, n, S), ...);
+    (farey_pair_step<T, K, P2>(x, n, S), ...);
 }
 
 template <typename T>
 struct Bin<HS_STD, T> {
+    template <bool P2>
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path, uint32_t j0) {
         float S[kHmax + 1];
 #pragma unroll
         for (int H = 0; H <= kHmax; ++H) S[H] = 0.f;
-        farey_all<T>(x, n, hmax, S, std::make_integer_sequence<int, kNumFrac>{});
+        farey_all<T, P2>(x, n, hmax, S, std::make_integer_sequence<int, kNumFrac>{});
 #pragma unroll
         for (int H = 1; H <= kHmax; ++H) {
             if (H <= hmax) {
+                if (P2 && !is_pow2(H)) {
+                    if (all_h) all_h[(size_t)(H - 1) * all_stride + n] = -INFINITY;  // not a stage
+                    continue;
+                }
                 float snr = calibrate(tb, S[H], H);
                 if (all_h) all_h[(size_t)(H - 1) * all_stride + n] = snr;
                 keep_best(snr, H, best, bh);
@@ -65,14 +72,16 @@ struct Bin<HS_STD, T> {
         }
     }
     // outputs n and n+1 (both < N); hmax == 32; no every-H table
+    template <bool P2>
     static __device__ __forceinline__ void eval_pair(const T* x, uint32_t n, const Tables& tb, float& best_a,
                                                      int& bh_a, float& best_b, int& bh_b) {
         float2 S[kHmax + 1];
 #pragma unroll
         for (int H = 0; H <= kHmax; ++H) S[H] = make_float2(0.f, 0.f);
-        farey_pair_all<T>(x, n, S, std::make_integer_sequence<int, kNumFrac>{});
+        farey_pair_all<T, P2>(x, n, S, std::make_integer_sequence<int, kNumFrac>{});
 #pragma unroll
         for (int H = 1; H <= kHmax; ++H) {
+            if (P2 && !is_pow2(H)) continue;
             keep_best(calibrate(tb, S[H].x, H), H, best_a, bh_a);
             keep_best(calibrate(tb, S[H].y, H), H, best_b, bh_b);
         }
@@ -122,6 +131,7 @@ __device__ __forceinline__ float window_max(const T* x, uint32_t N, uint32_t w0,
 // HS_FLAG_MAX_WINDOW0).
 template <typename T>
 struct Bin<HS_MAX, T> {
+    template <bool P2>
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path, uint32_t j0) {
@@ -130,8 +140,9 @@ struct Bin<HS_MAX, T> {
         for (int i = 1; i <= hv; ++i) {
             const uint32_t base = (uint32_t)i * n;
             S = __fadd_rn(S, window_max(x, N, base + j0, base + (uint32_t)i));
-            const float snr = calibrate(tb, S, i);
-            keep_best(snr, i, best, bh);
+            const bool stage = !P2 || is_pow2(i);
+            const float snr = stage ? calibrate(tb, S, i) : -INFINITY;
+            if (stage) keep_best(snr, i, best, bh);
             if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
         }
         if (all_h)
@@ -142,6 +153,7 @@ struct Bin<HS_MAX, T> {
 // Eq. 3: harmonic i adds x(i*n).  Harmonics run up to the bin's own valid count, four loads at a time.
 template <typename T>
 struct Bin<HS_FBIN, T> {
+    template <bool P2>
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path, uint32_t j0) {
@@ -155,8 +167,9 @@ struct Bin<HS_FBIN, T> {
             for (int k = 0; k < 4; ++k) {
                 if (i0 + k <= hv) {
                     S = __fadd_rn(S, v[k]);
-                    const float snr = calibrate(tb, S, i0 + k);
-                    keep_best(snr, i0 + k, best, bh);
+                    const bool stage = !P2 || is_pow2(i0 + k);
+                    const float snr = stage ? calibrate(tb, S, i0 + k) : -INFINITY;
+                    if (stage) keep_best(snr, i0 + k, best, bh);
                     if (all_h) all_h[(size_t)(i0 + k - 1) * all_stride + n] = snr;
                 }
             }
@@ -170,6 +183,7 @@ struct Bin<HS_FBIN, T> {
 // and then j grows by one.
 template <typename T>
 struct Bin<HS_GREEDY, T> {
+    template <bool P2>
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path, uint32_t j0) {
@@ -183,8 +197,9 @@ struct Bin<HS_GREEDY, T> {
             p |= (right ? 1u : 0u) << (i - 1);
             j += right ? 1u : 0u;
             S = __fadd_rn(S, right ? r : l);
-            const float snr = calibrate(tb, S, i);
-            keep_best(snr, i, best, bh);
+            const bool stage = !P2 || is_pow2(i);
+            const float snr = stage ? calibrate(tb, S, i) : -INFINITY;
+            if (stage) keep_best(snr, i, best, bh);
             if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
         }
         if (all_h)
@@ -196,7 +211,7 @@ struct Bin<HS_GREEDY, T> {
 // ------------------------------------------------------------------------------------------
 // One tile of output bins [t0, t1) of one spectrum; the whole block walks it in steps of kBlock.
 // ------------------------------------------------------------------------------------------
-template <int V, typename T>
+template <int V, typename T, bool P2>
 __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, uint32_t t1, const Tables& tb,
                                          const Work1d& w, const Out1d& o, size_t out_off, uint32_t spec,
                                          unsigned* status) {
@@ -207,7 +222,7 @@ __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, ui
             const uint32_t n = base + 2 * threadIdx.x;
             float ba = -INFINITY, bb = -INFINITY;
             int ha = 0, hb = 0;
-            Bin<HS_STD, T>::eval_pair(x, n, tb, ba, ha, bb, hb);
+            Bin<HS_STD, T>::template eval_pair<P2>(x, n, tb, ba, ha, bb, hb);
             o.best_snr[out_off + n] = ba;
             o.best_h[out_off + n] = (uint8_t)ha;
             o.best_snr[out_off + n + 1] = bb;
@@ -226,7 +241,7 @@ __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, ui
         int bh = 0;
         uint32_t path = 0;
         if (active) {
-            Bin<V, T>::eval(x, N, n, w.hmax, tb, o.all_h, N, best, bh, path,
+            Bin<V, T>::template eval<P2>(x, N, n, w.hmax, tb, o.all_h, N, best, bh, path,
                             (w.flags & HS_FLAG_MAX_WINDOW0) ? 0u : 1u);
             o.best_snr[out_off + n] = best;
             o.best_h[out_off + n] = (uint8_t)bh;
@@ -256,7 +271,7 @@ __device__ __forceinline__ const Tables& stage_tables(const Tables& tb, Tables& 
     return tb;
 }
 
-template <int V, typename T>
+template <int V, typename T, bool P2>
 __global__ void __launch_bounds__(kBlock, MinBlocks<V>::value) k_hs1d_single(const __grid_constant__ Tables tb_param,
                                                                             const Work1d w, const Out1d o,
                                                                             WsControl* ctl) {
@@ -266,7 +281,7 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<V>::value) k_hs1d_single(con
     uint32_t tile = (uint32_t)(kBlock * w.opt);
     uint32_t t0 = blockIdx.x * tile;
     uint32_t t1 = min(N, t0 + tile);
-    run_tile<V, T>((const T*)w.x, N, t0, t1, tb, w, o, 0, w.first_id, &ctl->status);
+    run_tile<V, T, P2>((const T*)w.x, N, t0, t1, tb, w, o, 0, w.first_id, &ctl->status);
 }
 
 // Tile prefix sums of a batch and reset of the work queue.  One block.  Offsets are absolute
@@ -324,7 +339,7 @@ __global__ void __launch_bounds__(1024) k_tile_scan(const int64_t* offsets, int 
 
 // Persistent kernel: CTAs pop (spectrum, tile) items in order from the queue.  The next item is
 // claimed while the current one is processed, so the atomic's round trip is off the critical path.
-template <int V, typename T>
+template <int V, typename T, bool P2>
 __global__ void __launch_bounds__(kBlock, MinBlocks<V>::value) k_hs1d_batched(const __grid_constant__ Tables tb_param,
                                                                              const Work1d w, const Out1d o,
                                                                              WsControl* ctl, const int64_t* prefix) {
@@ -350,8 +365,8 @@ __global__ void __launch_bounds__(kBlock, MinBlocks<V>::value) k_hs1d_batched(co
         const uint32_t N = (uint32_t)(w.offsets[s + 1] - off);
         const uint32_t t0 = (uint32_t)(item - (unsigned long long)prefix[s]) * tile;
         const uint32_t t1 = min(N, t0 + tile);
-        run_tile<V, T>((const T*)w.x + off, N, t0, t1, tb, w, o, (size_t)off, w.first_id + (uint32_t)s,
-                       &ctl->status);
+        run_tile<V, T, P2>((const T*)w.x + off, N, t0, t1, tb, w, o, (size_t)off, w.first_id + (uint32_t)s,
+                           &ctl->status);
         __syncthreads();  // every thread has read s_item / s_spec
         if (threadIdx.x == 0) {
             s_item = next;
@@ -369,53 +384,67 @@ void launch_tile_scan(const int64_t* offsets, int n_spectra, int64_t tile, int64
     k_tile_scan<<<1, 1024, 0, s>>>(offsets, n_spectra, tile, max_bins, elem_bytes, prefix, ctl);
 }
 
-template <int V, typename T>
+template <int V, typename T, bool P2>
 static int& occupancy_slot() {
     static int occ = 0;  // resident CTAs per SM of the persistent kernel
     return occ;
 }
 
-template <int V, typename T>
+template <int V, typename T, bool P2>
 static int occupancy() {
-    int& oc = occupancy_slot<V, T>();
+    int& oc = occupancy_slot<V, T, P2>();
     if (oc == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_hs1d_batched<V, T>, kBlock, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_hs1d_batched<V, T, P2>, kBlock, 0);
         if (e != cudaSuccess || oc < 1) oc = 1;
     }
     return oc;
 }
 
-template <int V, typename T>
+template <int V, typename T, bool P2>
 static cudaError_t launch_typed(const Tables& tab, const Work1d& w, const Out1d& o, WsControl* ctl,
                                 int64_t* prefix, int sm_count, cudaStream_t s) {
     const int64_t tile = (int64_t)kBlock * w.opt;
     if (w.offsets == nullptr) {
         if (w.n_bins == 0) return cudaSuccess;
         unsigned grid = (unsigned)((w.n_bins + tile - 1) / tile);
-        k_hs1d_single<V, T><<<grid, kBlock, 0, s>>>(tab, w, o, ctl);
+        k_hs1d_single<V, T, P2><<<grid, kBlock, 0, s>>>(tab, w, o, ctl);
         return cudaGetLastError();
     }
     launch_tile_scan(w.offsets, w.n_spectra, tile, w.max_bins, (int)sizeof(T), prefix, ctl, s);
-    k_hs1d_batched<V, T><<<(unsigned)(sm_count * occupancy<V, T>()), kBlock, 0, s>>>(tab, w, o, ctl, prefix);
+    k_hs1d_batched<V, T, P2><<<(unsigned)(sm_count * occupancy<V, T, P2>()), kBlock, 0, s>>>(tab, w, o, ctl,
+                                                                                          prefix);
     return cudaGetLastError();
 }
 
 template <int V>
 static cudaError_t launch_dtype(hs_dtype dt, const Tables& tab, const Work1d& w, const Out1d& o, WsControl* ctl,
                                 int64_t* prefix, int sm_count, cudaStream_t s) {
+    const bool p2 = (w.flags & HS_FLAG_POW2_STAGES) != 0;
     switch (dt) {
-        case HS_F32: return launch_typed<V, float>(tab, w, o, ctl, prefix, sm_count, s);
-        case HS_F16: return launch_typed<V, __half>(tab, w, o, ctl, prefix, sm_count, s);
-        case HS_BF16: return launch_typed<V, __nv_bfloat16>(tab, w, o, ctl, prefix, sm_count, s);
+        case HS_F32:
+            return p2 ? launch_typed<V, float, true>(tab, w, o, ctl, prefix, sm_count, s)
+                      : launch_typed<V, float, false>(tab, w, o, ctl, prefix, sm_count, s);
+        case HS_F16:
+            return p2 ? launch_typed<V, __half, true>(tab, w, o, ctl, prefix, sm_count, s)
+                      : launch_typed<V, __half, false>(tab, w, o, ctl, prefix, sm_count, s);
+        case HS_BF16:
+            return p2 ? launch_typed<V, __nv_bfloat16, true>(tab, w, o, ctl, prefix, sm_count, s)
+                      : launch_typed<V, __nv_bfloat16, false>(tab, w, o, ctl, prefix, sm_count, s);
     }
     return cudaErrorInvalidValue;
 }
 
+template <int V, bool P2>
+static void warm_p(hs_dtype dt) {
+    if (dt == HS_F32) occupancy<V, float, P2>();
+    if (dt == HS_F16) occupancy<V, __half, P2>();
+    if (dt == HS_BF16) occupancy<V, __nv_bfloat16, P2>();
+}
+
 template <int V>
 static void warm_v(hs_dtype dt) {
-    if (dt == HS_F32) occupancy<V, float>();
-    if (dt == HS_F16) occupancy<V, __half>();
-    if (dt == HS_BF16) occupancy<V, __nv_bfloat16>();
+    warm_p<V, false>(dt);
+    warm_p<V, true>(dt);
 }
 
 // Query occupancy outside any stream capture.

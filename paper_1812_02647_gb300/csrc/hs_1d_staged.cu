@@ -451,7 +451,8 @@ cudaError_t launch_typed(const Tables& tab, const Work1d& w, const Out1d& o, WsC
 }  // namespace
 
 bool eq1_staged_applies(const Work1d& w, const Out1d& o) {
-    return w.offsets != nullptr && w.hmax == kHmax && o.all_h == nullptr && o.path == nullptr;
+    return w.offsets != nullptr && w.hmax == kHmax && o.all_h == nullptr && o.path == nullptr &&
+           (w.flags & HS_FLAG_POW2_STAGES) == 0;
 }
 
 void warm_eq1_staged(hs_dtype dt) {

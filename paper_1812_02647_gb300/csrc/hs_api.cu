@@ -18,6 +18,8 @@ using namespace hs;
 
 namespace {
 
+constexpr int kPlanFlags = HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS | HS_FLAG_MAX_WINDOW0 | HS_FLAG_POW2_STAGES;
+
 bool single_variant(int v) { return v == HS_STD || v == HS_MAX || v == HS_FBIN || v == HS_GREEDY; }
 
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
@@ -98,7 +100,7 @@ hs_status hs_plan_create(hs_plan** plan, const hs_plan_desc* d) {
     if (d->hmax < 1 || d->hmax > hcap) return HS_ERR_INVALID;
     if (d->max_bins < 0 || d->max_bins > HS_MAX_BINS_1D) return HS_ERR_INVALID;
     if (d->nz > 0 && (d->z_min > 0 || d->z_min + d->nz - 1 < 0 || d->nz > 32767)) return HS_ERR_INVALID;
-    if (d->cand_capacity < 0 || (d->flags & ~(HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS | HS_FLAG_MAX_WINDOW0)) != 0) return HS_ERR_INVALID;
+    if (d->cand_capacity < 0 || (d->flags & ~kPlanFlags) != 0 || (d->nz != 0 && (d->flags & HS_FLAG_POW2_STAGES))) return HS_ERR_INVALID;
     if (std::isnan(d->threshold)) return HS_ERR_INVALID;
     hs_plan* p = new (std::nothrow) hs_plan;
     if (!p) return HS_ERR_NOMEM;
@@ -149,7 +151,7 @@ hs_status hs_noise_calibration(hs_variant v, int hmax, float* mu, float* isig) {
 
 hs_status hs_noise_calibration_flags(hs_variant v, int hmax, int flags, float* mu, float* isig) {
     if (!single_variant(v) || !mu || !isig || hmax < 1 || hmax > HS_HMAX_1D) return HS_ERR_INVALID;
-    if ((flags & ~(HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS | HS_FLAG_MAX_WINDOW0)) != 0) return HS_ERR_INVALID;
+    if ((flags & ~kPlanFlags) != 0) return HS_ERR_INVALID;
     const int extra = (flags & HS_FLAG_MAX_WINDOW0) ? 1 : 0;  // Eq. 2 window of i + extra bins
     // standardised Exp(1) noise, bins far enough from 0 that every read is a distinct bin
     double hn = 0.0, hn2 = 0.0, mean_sum = 0.0, var_sum = 0.0;

@@ -43,20 +43,29 @@ __device__ __forceinline__ uint32_t frac_index(uint32_t n) {
     return __umulhi(n, F) + ((n * F) >> 31);
 }
 
-// Generic hmax: one output per call, harmonics beyond hmax skipped.
-template <typename T, int K>
-__device__ __forceinline__ void farey_step(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1]) {
-    constexpr Frac f = farey_at(K);
-    const float v = widen<T>(__ldg(x + frac_index<f.p, f.q>(n)));
-#pragma unroll
-    for (int m = 1; m * f.q <= kHmax; ++m)
-        if (m * f.q <= hmax) S[m * f.q] = __fadd_rn(S[m * f.q], v);
+// Power-of-two stages (HS_FLAG_POW2_STAGES): only H = 1, 2, 4, .. are searched.  A stage H = m q
+// of fraction p/q needs q and m to be powers of two, so Eq. 1 then reads only the fractions i/32.
+__host__ __device__ constexpr bool is_pow2(int v) {
+    return (v & (v - 1)) == 0;
 }
 
-template <typename T, int... K>
+// Generic hmax: one output per call, harmonics beyond hmax skipped (and, with P2, every H that is
+// not a stage).
+template <typename T, int K, bool P2 = false>
+__device__ __forceinline__ void farey_step(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1]) {
+    constexpr Frac f = farey_at(K);
+    if constexpr (!P2 || is_pow2(f.q)) {
+        const float v = widen<T>(__ldg(x + frac_index<f.p, f.q>(n)));
+#pragma unroll
+        for (int m = 1; m * f.q <= kHmax; ++m)
+            if ((!P2 || is_pow2(m)) && m * f.q <= hmax) S[m * f.q] = __fadd_rn(S[m * f.q], v);
+    }
+}
+
+template <typename T, bool P2 = false, int... K>
 __device__ __forceinline__ void farey_all(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1],
                                           std::integer_sequence<int, K...>) {
-    (farey_step<T, K>(x, n, hmax, S), ...);  // in increasing fraction order
+    (farey_step<T, K, P2>(x, n, hmax, S), ...);  // in increasing fraction order
 }
 
 }  // namespace hs

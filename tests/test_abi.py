@@ -43,7 +43,8 @@ def test_status_strings(hs_lib):
 @pytest.mark.parametrize("bad", [dict(variants=0), dict(variants=16), dict(hmax=0), dict(hmax=33),
                                  dict(dtype=3), dict(max_bins=-1), dict(max_bins=(1 << 26) + 1),
                                  dict(nz=5, z_min=1, hmax=16), dict(nz=5, z_min=-5, hmax=16),
-                                 dict(nz=5, z_min=-2, hmax=17), dict(cand_capacity=-1), dict(flags=8),
+                                 dict(nz=5, z_min=-2, hmax=17), dict(cand_capacity=-1), dict(flags=16),
+                                 dict(nz=5, z_min=-2, hmax=16, flags=8),
                                  dict(threshold=float("nan"))])
 def test_plan_create_rejects(hs_lib, bad):
     kw = dict(variants=0xF, hmax=32, dtype=0, max_bins=1 << 20, nz=0, z_min=0, threshold=6.0, cand_capacity=0,

@@ -390,6 +390,34 @@ def test_backward_matches_oracle_gradient(hs_lib, torch, variant):
     np.testing.assert_allclose(grad, exp, rtol=1e-5, atol=1e-6)
 
 
+# ---- power-of-two stages (HS_FLAG_POW2_STAGES), against the oracle's pow2 mode ----
+
+@pytest.mark.parametrize("variant", VARIANTS)
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_pow2_stages_bit_exact(hs_lib, torch, variant, dtype):
+    x, _ = hs_synth.spectrum_1d_pulsar()
+    xd, xw = _widen(torch, x, dtype)
+    code = {"f32": 0, "bf16": 2}[dtype]
+    hs, mu, isig = _make(hs_lib, variant, True, dtype=code, flags=hs_lib.FLAG_OUT_ALL_H | hs_lib.FLAG_POW2_STAGES)
+    o = hs.sum_1d(variant, xd, all_h=True)
+    r = oracle.hs_1d(variant, xw, hmax=32, mu=mu, isig=isig, all_h=True, pow2=True, nthreads=8)
+    np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    # the fast paths (no every-H table): single spectrum and a batch
+    hs2, _, _ = _make(hs_lib, variant, True, dtype=code, flags=hs_lib.FLAG_POW2_STAGES, max_spectra=3)
+    o2 = hs2.sum_1d(variant, xd)
+    np.testing.assert_array_equal(o2["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o2["best_h"].cpu().numpy(), r["best_h"])
+    _check_candidates(hs_lib, o2, r["best_snr"], r["best_h"])
+    n = x.size
+    offsets = np.array([0, 4096, 4096 + 8, n // 8 * 8], np.int64)
+    ob = hs2.sum_batched(variant, xd, torch.from_numpy(offsets).cuda())
+    rb = oracle.hs_batched(variant, xw, offsets, mu=mu, isig=isig, pow2=True, nthreads=8)
+    np.testing.assert_array_equal(ob["best_snr"].cpu().numpy()[: offsets[-1]], rb["best_snr"])
+    np.testing.assert_array_equal(ob["best_h"].cpu().numpy()[: offsets[-1]], rb["best_h"])
+
+
 # ---- Eq. 2 with the window j = 0..i (HS_FLAG_MAX_WINDOW0), against the oracle's "max0" ----
 
 def _max0(hs_lib, dtype=0, max_spectra=1, flags=0):

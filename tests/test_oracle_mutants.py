@@ -39,15 +39,15 @@ MUTANTS = [
     ("freq-bin reads the neighbour", "hs_oracle_body.h", "S = S + x[(int64_t)H * n];",
      "S = S + x[(int64_t)H * n + (H > 1)];", ["test_golden_1d_hand_worked", "test_delta_spike_fbin"]),
     ("largest H wins ties", "hs_oracle_body.h",
-     "if (snr > best) {\n                best = snr;\n                best_h = H;",
-     "if (snr >= best) {\n                best = snr;\n                best_h = H;", ["test_zero_spectrum_tie_break"]),
+     "if (snr > best) {\n                    best = snr;\n                    best_h = H;",
+     "if (snr >= best) {\n                    best = snr;\n                    best_h = H;", ["test_zero_spectrum_tie_break"]),
     ("max/greedy range off by one", "hs_oracle.c", "lim = (N - 1) / (n + 1); /* H*(n+1) <= N-1 */",
      "lim = N / (n + 1);", ["test_range_limits"]),
     ("2-D z rounded toward zero", "hs_oracle.c", "return (a % b != 0 && a < 0) ? q - 1 : q;", "return q;",
      ["test_golden_2d_hand_worked", "test_delta_spike_2d_negative_half_rounding"]),
     ("calibration applied in the wrong order", "hs_oracle_body.h",
-     "REAL h = sum * cs[H];\n            snr = (h - mu[H]) * isig[H];",
-     "REAL h = sum * cs[H];\n            snr = h * isig[H] - mu[H];", ["test_calibration_closed_form"]),
+     "REAL h = sum * cs[H];\n                snr = (h - mu[H]) * isig[H];",
+     "REAL h = sum * cs[H];\n                snr = h * isig[H] - mu[H];", ["test_calibration_closed_form"]),
     ("2-D transposed plane index", "hs_oracle_body.h",
      "sum = sum + plane[(zi - z_min) * row_stride + ni];", "sum = sum + plane[ni * nz + (zi - z_min)];",
      ["test_2d_zero_row_is_1d_eq1", "test_golden_2d_hand_worked"]),
@@ -55,6 +55,10 @@ MUTANTS = [
      "double w = g[n] * isig;", ["test_adjoint_is_transpose_of_linear_map"]),
     ("max adjoint routes to the last maximum", "hs_oracle.c", "if (x[base + jj] > x[m]) m = base + jj;",
      "if (x[base + jj] >= x[m]) m = base + jj;", ["test_adjoint_max_ties_route_to_first_maximum"]),
+    ("every H is a power-of-two stage", "hs_oracle_body.h", "const int stage = !pow2 || (H & (H - 1)) == 0;",
+     "const int stage = 1;", ["test_pow2_stages_restrict_the_full_search"]),
+    ("odd H are stages", "hs_oracle_body.h", "const int stage = !pow2 || (H & (H - 1)) == 0;",
+     "const int stage = !pow2 || (H & 1) == 0 || H == 1;", ["test_pow2_stages_restrict_the_full_search"]),
     ("f16 ties round away from zero", "hs_oracle.c", "uint32_t h = (r + 0x0FFFu + ((r >> 13) & 1u)) >> 13;",
      "uint32_t h = (r + 0x1000u) >> 13;", ["test_standardize_cast_f16_matches_ieee_library"]),
     ("bf16 truncates", "hs_oracle.c", "return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);",
@@ -88,6 +92,7 @@ def _run_pin(name):
               "test_range_limits": [(v,) for v in pins.VARIANTS],
               "test_linearity": [("std",), ("fbin",)],
               "test_calibration_closed_form": [(v,) for v in pins.VARIANTS],
+              "test_pow2_stages_restrict_the_full_search": [(v,) for v in pins.VARIANTS],
               "test_adjoint_is_transpose_of_linear_map": [("std",), ("fbin",)]}
     for args in params.get(name, [()]):
         fn(*args)

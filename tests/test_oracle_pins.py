@@ -539,3 +539,30 @@ def test_sampled_entry_points_match_full():
     part = oracle.hs_2d_cells(plane, -4, rows, bins)
     np.testing.assert_array_equal(part["best_snr"], full["best_snr"][rows, bins])
     np.testing.assert_array_equal(part["best_h"], full["best_h"][rows, bins])
+
+
+# ---------------------------------------------------------------------------------------------
+# power-of-two stages (variant flag): a restriction of the full search
+# ---------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_pow2_stages_restrict_the_full_search(variant):
+    """With only H = 1, 2, 4, .. searched, every stage's snr is the full search's, the other H read
+    -inf, and the best H is the first stage with the largest snr (numpy argmax over the stages)."""
+    N, hmax = 3000, 32
+    x = rand_spectrum(N, 41)
+    mu, isig = oracle.noise_calibration(variant, hmax)
+    full = oracle.hs_1d(variant, x, hmax=hmax, mu=mu, isig=isig, all_h=True)
+    p2 = oracle.hs_1d(variant, x, hmax=hmax, mu=mu, isig=isig, all_h=True, pow2=True)
+    stages = [1, 2, 4, 8, 16, 32]
+    others = [h for h in range(1, hmax + 1) if h not in stages]
+    np.testing.assert_array_equal(p2["all_h"][[h - 1 for h in stages]], full["all_h"][[h - 1 for h in stages]])
+    assert np.isneginf(p2["all_h"][[h - 1 for h in others]]).all()
+    sub = full["all_h"][[h - 1 for h in stages]]
+    valid = np.isfinite(sub).any(axis=0)
+    k = np.argmax(np.where(np.isfinite(sub), sub, -np.inf), axis=0)
+    np.testing.assert_array_equal(p2["best_h"][valid], np.array(stages)[k[valid]])
+    np.testing.assert_array_equal(p2["best_snr"][valid], sub[k[valid], np.nonzero(valid)[0]])
+    assert (p2["best_h"][~valid] == 0).all()
+    if variant == "greedy":
+        np.testing.assert_array_equal(p2["path"], full["path"])  # the recursion itself is unchanged
