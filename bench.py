@@ -298,6 +298,28 @@ def secondary(torch, hs, stream, tiles=None, reps=2):
     del p, mu, sd, od
     torch.cuda.empty_cache()
 
+    # the step before the sums: power of complex spectra, block-median dereddening (128 bins),
+    # standardisation, FP16 store; 1024 spectra x 2^20 complex bins (8 GiB in, 2 GiB out)
+    n_s, n_b = 1024, 1 << 20
+    g = torch.Generator(device="cuda")
+    g.manual_seed(6000)
+    spec = torch.randn(2 * n_s * n_b, generator=g, device="cuda").mul_(0.7071067811865476)
+    od = torch.arange(n_s + 1, device="cuda", dtype=torch.int64) * n_b
+    hu = hs.HarmonicSum(variants=hs.STD, dtype=hs.F16, max_bins=n_b, max_spectra=n_s)
+    med = torch.empty(n_s * n_b // 128, device="cuda")
+    out16 = torch.empty(n_s * n_b, dtype=torch.float16, device="cuda")
+    ms = _time_ms(torch, stream, lambda: hs.hs_power_normalize(hu.plan, spec, od, 0, 128, med, out16, hu.ws, stream),
+                  reps)
+    compulsory = n_s * n_b * (8 + 2)  # complex in, FP16 out
+    moved = n_s * n_b * (8 + 8 + 2)  # the median pass and the normalising pass each read the input
+    peaks, _ = load_peaks()
+    out["upstream"] = {"workload": "1024 spectra x 2^20 complex bins -> FP16, blocks of 128 bins",
+                       "ms": ms, "gbs_compulsory": compulsory / (ms / 1e3) / 1e9,
+                       "gbs_moved": moved / (ms / 1e3) / 1e9,
+                       "frac_compulsory_of_hbm": compulsory / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    del spec, od, hu, med, out16
+    torch.cuda.empty_cache()
+
     # differentiation: 256 spectra x 2^20, Eq. 1 and Max, loss = sum softplus(snr - 5)
     n_s, n_b = 256, 1 << 20
     total = n_s * n_b

@@ -240,6 +240,25 @@ hs_status hs_standardize_cast(const float* d_p, const int64_t* d_offsets, int n_
                               const float* d_mu, const float* d_sigma, hs_dtype dst_dtype, void* d_out,
                               cudaStream_t stream);
 
+/* ---- the step before the sums: power, dereddening, standardisation -------------------------- */
+
+/* The input of the sums from a complex spectrum (the paper sums a power spectrum and does not say how
+ * it is normalised; this is the block-median reading):
+ *   P_k = re_k^2 + im_k^2 (FP32);  m_j = the lower median of P over block j of `block` bins (rank
+ *   floor((size - 1)/2)); base_k = the straight line between the centres of the two nearest blocks
+ *   (flat before the first centre and after the last); x_k = P_k ln2 / base_k - 1 (Exp-distributed
+ *   power has mean median / ln 2), 0 where base_k <= 0; stored in the plan's dtype (RNE).
+ * d_spec: device float pairs (re, im); spectrum s holds complex bins [offsets[s], offsets[s+1]) of
+ * the packed batch (16-byte aligned starts: even offsets), or, with d_offsets NULL, one spectrum of
+ * n_bins.  block: 32, 64, 128 or 256.  d_medians: device float[medians_capacity] receiving the
+ * block medians, spectrum s's from sum_{r<s} ceil(len_r / block) on; a batch whose medians do not
+ * fit is reported by hs_sync_status (HS_ERR_INVALID) and its spectra left unwritten.  d_out: the
+ * plan's dtype, packed like d_spec (one value per complex bin), ready for hs_sum_batched.  The
+ * workspace is the plan's (hs_plan_workspace_size for n_spectra). */
+hs_status hs_power_normalize(const hs_plan* plan, const float* d_spec, const int64_t* d_offsets, int n_spectra,
+                             int64_t n_bins, int block, float* d_medians, int64_t medians_capacity, void* d_out,
+                             void* d_ws, size_t ws_bytes, cudaStream_t stream);
+
 /* ---- candidates ------------------------------------------------------------------------- */
 
 /* Sort the first min(count, capacity) candidates in place by (variant, spectrum, z, bin), on the

@@ -60,6 +60,7 @@ def _load():
         lib.hs_oracle_grad_f64.argtypes = [I, P, I64, I, P, P, P, P]
         lib.hs_oracle_standardize_cast.argtypes = [P, I64, ctypes.c_float, ctypes.c_float, I, P]
         lib.hs_oracle_noise_moments.argtypes = [I, I, P, P]
+        lib.hs_oracle_power_normalize.argtypes = [P, I64, I, I, P, P]
         lib.hs_oracle_max_threads.restype = I
         _lib = lib
     return _lib
@@ -217,6 +218,22 @@ def standardize_cast(p, mu: float, sigma: float, dtype: str):
     code = {"f16": 1, "bf16": 2}[dtype]
     _load().hs_oracle_standardize_cast(_ptr(p), p.size, float(mu), float(sigma), code, _ptr(out))
     return out
+
+
+def power_normalize(spec, block: int, dtype: str = "f32"):
+    """Power of a complex spectrum (complex64, or float32 interleaved re/im), divided by the
+    interpolated block-median estimate of its local mean and standardised; FP32 values, or the
+    uint16 bit patterns of FP16/BF16.  Returns (x, block medians)."""
+    s = np.ascontiguousarray(spec)
+    if np.iscomplexobj(s):
+        s = np.ascontiguousarray(s.astype(np.complex64)).view(np.float32)
+    s = np.ascontiguousarray(s, dtype=np.float32)
+    n = s.size // 2
+    code = {"f32": 0, "f16": 1, "bf16": 2}[dtype]
+    out = np.empty(n, np.float32 if code == 0 else np.uint16)
+    med = np.empty(max(1, (n + block - 1) // block), np.float32)
+    _load().hs_oracle_power_normalize(_ptr(s), n, int(block), code, _ptr(out), _ptr(med))
+    return out, med[: (n + block - 1) // block]
 
 
 def noise_moments(variant, hmax: int = 32):

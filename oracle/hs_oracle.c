@@ -18,6 +18,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdlib.h>
 #include <string.h>
 #ifdef _OPENMP
 #include <omp.h>
@@ -148,6 +149,75 @@ void hs_oracle_standardize_cast(const float* p, int64_t n, float mu, float sigma
         float y = (p[k] - mu) / sigma;
         out[k] = (dtype == 1) ? f32_to_f16_rne(y) : f32_to_bf16_rne(y);
     }
+}
+
+/*
+ * The step before the harmonic sum (the sums of Section 2 run on a power spectrum): the power of a
+ * complex spectrum, divided by a running estimate of its local mean, standardised, and stored as
+ * FP32 (dtype 0), FP16 (1) or BF16 (2).  Reading (the paper does not describe its normalisation):
+ * block medians, robust to the pulsar's own harmonics, as in PRESTO-style dereddening.
+ *   P_k = re_k re_k + im_k im_k                             FP32, each operation rounded
+ *   m_j = the lower median of P over block j = [jB, min(N, jB + B)): rank floor((size_j - 1)/2)
+ *   Exp-distributed power has mean median / ln 2; between block centres c_j = jB + h_j,
+ *   h_j = (size_j - 1)/2, the median is interpolated linearly.  For bin k in block j, d = k - jB:
+ *     d >= h_j, j + 1 < J:  t = (d - h_j) / (B - h_j + h_{j+1}),      a = m_j,     b = m_{j+1}
+ *     d <  h_j, j > 0:      t = (d + B - h_{j-1}) / (B - h_{j-1} + h_j), a = m_{j-1}, b = m_j
+ *     otherwise (before the first centre, after the last): base = m_j
+ *     base = a + t (b - a)
+ *   x_k = (P_k ln2) / base - 1, and 0 where base <= 0 (a block with no power).
+ * medians (optional) receives m_j, j = 0..ceil(N/B)-1.
+ */
+static int hs_oracle_cmp_float(const void* a, const void* b) {
+    float x = *(const float*)a, y = *(const float*)b;
+    return (x > y) - (x < y);
+}
+
+void hs_oracle_power_normalize(const float* spec, int64_t n, int block, int dtype, void* out, float* medians) {
+    const float ln2 = 0.693147180559945309417232f;
+    int64_t nblk = (n + block - 1) / block;
+    float* P = (float*)malloc(sizeof(float) * (size_t)(n > 0 ? n : 1));
+    float* m = (float*)malloc(sizeof(float) * (size_t)(nblk > 0 ? nblk : 1));
+    float* tmp = (float*)malloc(sizeof(float) * (size_t)block);
+    for (int64_t k = 0; k < n; ++k) {
+        float re = spec[2 * k], im = spec[2 * k + 1];
+        float a = re * re;
+        float b = im * im;
+        P[k] = a + b;
+    }
+    for (int64_t j = 0; j < nblk; ++j) {
+        int64_t lo = j * block, size = (n - lo < block) ? n - lo : block;
+        memcpy(tmp, P + lo, sizeof(float) * (size_t)size);
+        qsort(tmp, (size_t)size, sizeof(float), hs_oracle_cmp_float);
+        m[j] = tmp[(size - 1) / 2];
+        if (medians) medians[j] = m[j];
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t j = k / block;
+        float d = (float)(k - j * block);
+        int64_t size_j = (n - j * block < block) ? n - j * block : block;
+        float hj = 0.5f * (float)(size_j - 1);
+        float base;
+        if (d >= hj && j + 1 < nblk) {
+            int64_t size_n = (n - (j + 1) * block < block) ? n - (j + 1) * block : block;
+            float hn = 0.5f * (float)(size_n - 1);
+            float t = (d - hj) / ((float)block - hj + hn);
+            base = m[j] + t * (m[j + 1] - m[j]);
+        } else if (d < hj && j > 0) {
+            float hp = 0.5f * (float)(block - 1); /* block j-1 is full */
+            float t = (d + (float)block - hp) / ((float)block - hp + hj);
+            base = m[j - 1] + t * (m[j] - m[j - 1]);
+        } else {
+            base = m[j];
+        }
+        float x = base > 0.0f ? (P[k] * ln2) / base - 1.0f : 0.0f;
+        if (dtype == 0)
+            ((float*)out)[k] = x;
+        else
+            ((uint16_t*)out)[k] = dtype == 1 ? f32_to_f16_rne(x) : f32_to_bf16_rne(x);
+    }
+    free(P);
+    free(m);
+    free(tmp);
 }
 
 /*

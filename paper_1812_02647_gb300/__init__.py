@@ -75,6 +75,7 @@ def _load():
         "hs_sum_2d": ([_P, _P, I64, I64, U32, ctypes.POINTER(Out2d), _P, SZ, _P], I),
         "hs_backward": ([_P, I, _P, _P, I, I64, _P, _P, _P, _P, _P], I),
         "hs_standardize_cast": ([_P, _P, I, I64, _P, _P, I, _P, _P], I),
+        "hs_power_normalize": ([_P, _P, _P, I, I64, I, _P, I64, _P, _P, SZ, _P], I),
         "hs_sort_candidates": ([_P, _P, I64, _P, _P, SZ, _P], I),
         "hs_graph_create_batched": ([_P, I, _P, _P, I, U32, _P, _P, SZ, _P, ctypes.POINTER(_P)], I),
         "hs_graph_launch": ([_P, _P], I),
@@ -215,6 +216,16 @@ def hs_sort_candidates(cand, cand_count, tmp, ws, stream=None):
     cap = cand.numel() // 16
     return _check(_lib.hs_sort_candidates(_ptr(cand), _ptr(cand_count), cap, _ptr(tmp), _ptr(ws), ws.numel(),
                                           _stream(stream)), "hs_sort_candidates")
+
+
+def hs_power_normalize(plan, spec, offsets, n_bins, block, medians, out, ws, stream=None):
+    """Power of complex spectra (``spec``: float32 pairs re, im, or complex64), dereddened by block
+    medians and standardised into ``out`` (the plan's dtype).  ``offsets`` None: one spectrum of
+    ``n_bins`` complex bins."""
+    n_spectra = 1 if offsets is None else offsets.numel() - 1
+    return _check(_lib.hs_power_normalize(plan, _ptr(spec), _ptr(offsets), n_spectra, int(n_bins), int(block),
+                                          _ptr(medians), medians.numel(), _ptr(out), _ptr(ws), ws.numel(),
+                                          _stream(stream)), "hs_power_normalize")
 
 
 def hs_graph_create_batched(plan, variant_mask, x, offsets, outs, ws, first_id=0, stream=None):

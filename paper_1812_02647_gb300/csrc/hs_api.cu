@@ -302,6 +302,29 @@ hs_status hs_backward(const hs_plan* p, hs_variant v, const void* d_x, const int
                                       p->d.hmax, p->d.flags, d_grad_snr, d_best_h, d_path, d_grad_x, stream));
 }
 
+hs_status hs_power_normalize(const hs_plan* p, const float* d_spec, const int64_t* d_offsets, int n_spectra,
+                             int64_t n_bins, int block, float* d_medians, int64_t medians_capacity, void* d_out,
+                             void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!p || p->d.nz != 0 || !d_spec || !d_medians || !d_out || medians_capacity < 0) return HS_ERR_INVALID;
+    if (block != 32 && block != 64 && block != 128 && block != 256) return HS_ERR_INVALID;
+    if (!aligned(d_spec, 16) || !aligned(d_medians, 4) || !aligned(d_out, 16)) return HS_ERR_ALIGN;
+    if (d_offsets) {
+        if (n_spectra < 0 || n_spectra > 65535 || !aligned(d_offsets, 8)) return HS_ERR_INVALID;
+    } else {
+        if (n_bins < 0 || n_bins > p->d.max_bins) return HS_ERR_INVALID;
+        n_spectra = 1;
+    }
+    hs_status st = check_ws(p, n_spectra, d_ws, ws_bytes);
+    if (st != HS_OK) return st;
+    if (n_spectra == 0 || (!d_offsets && n_bins == 0)) return HS_OK;
+    if ((st = ensure_sm_count(p)) != HS_OK) return st;
+    WsControl* ctl = reinterpret_cast<WsControl*>(d_ws);
+    int64_t* prefix = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(d_ws) + kWsControlBytes);
+    return check_cuda(launch_power_normalize(d_spec, d_offsets, n_spectra, n_bins, block, d_medians,
+                                             (long long)medians_capacity, p->d.dtype, d_out, p->d.max_bins,
+                                             p->sm_count, prefix, ctl, stream));
+}
+
 hs_status hs_standardize_cast(const float* d_p, const int64_t* d_offsets, int n_spectra, int64_t n_bins,
                               const float* d_mu, const float* d_sigma, hs_dtype dst, void* d_out,
                               cudaStream_t stream) {

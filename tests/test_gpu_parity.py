@@ -554,3 +554,68 @@ def test_batch_slice_with_absolute_offsets(hs_lib, torch):
     assert torch.equal(part["best_snr"][a:], full["best_snr"][a:])
     assert bool((part["best_snr"][:a] == 7.0).all())
     assert hs.sync_status() == hs_lib.OK
+
+
+# ---- the step before the sums: power, block-median dereddening, standardisation ----
+
+def _complex_batch(lens, seed):
+    rng = np.random.default_rng(seed)
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    k = np.arange(offsets[-1])
+    trend = 1.0 + 50.0 / (1.0 + (k % 100000) / 30.0)
+    z = (rng.standard_normal(offsets[-1]) + 1j * rng.standard_normal(offsets[-1])) * np.sqrt(trend / 2.0)
+    return z.astype(np.complex64), offsets
+
+
+@pytest.mark.parametrize("block", [32, 64, 128, 256])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_power_normalize_bit_exact(hs_lib, torch, block, dtype):
+    lens = [0, 2, 64, 1000, 4096 + 22, 100000, 256, 30, 1 << 17]
+    z, offsets = _complex_batch(lens, 17 + block)
+    code = {"f32": 0, "f16": 1, "bf16": 2}[dtype]
+    hs = hs_lib.HarmonicSum(variants=hs_lib.STD, dtype=code, max_bins=1 << 18, max_spectra=len(lens))
+    spec = torch.from_numpy(z.view(np.float32)).cuda()
+    od = torch.from_numpy(offsets).cuda()
+    nmed = sum((l + block - 1) // block for l in lens)
+    med = torch.full((nmed,), -1.0, device="cuda")
+    tdt = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    out = torch.empty(offsets[-1], dtype=tdt, device="cuda")
+    hs_lib.hs_power_normalize(hs.plan, spec, od, 0, block, med, out, hs.ws)
+    assert hs.sync_status() == hs_lib.OK
+    got = out.cpu().view(torch.int16 if dtype != "f32" else torch.float32).numpy()
+    gm = med.cpu().numpy()
+    moff = 0
+    for s in range(len(lens)):
+        a, b = offsets[s], offsets[s + 1]
+        if b == a:
+            continue
+        x, m = oracle.power_normalize(z[a:b], block, dtype)
+        np.testing.assert_array_equal(gm[moff:moff + m.size], m)
+        if dtype == "f32":
+            np.testing.assert_array_equal(got[a:b], x)
+        else:
+            np.testing.assert_array_equal(got[a:b].view(np.uint16), x)
+        moff += m.size
+
+
+def test_power_normalize_single_and_errors(hs_lib, torch):
+    z, _ = _complex_batch([50000], 5)
+    hs = hs_lib.HarmonicSum(variants=hs_lib.STD, max_bins=1 << 16)
+    spec = torch.from_numpy(z.view(np.float32)).cuda()
+    med = torch.empty(50000 // 128 + 1, device="cuda")
+    out = torch.empty(50000, device="cuda")
+    hs_lib.hs_power_normalize(hs.plan, spec, None, 50000, 128, med, out, hs.ws)
+    assert hs.sync_status() == hs_lib.OK
+    x, m = oracle.power_normalize(z, 128)
+    np.testing.assert_array_equal(out.cpu().numpy(), x)
+    np.testing.assert_array_equal(med.cpu().numpy(), m)
+    # a median array one entry short: nothing written for that spectrum, reported by the status word
+    hb = hs_lib.HarmonicSum(variants=hs_lib.STD, max_bins=1 << 16, max_spectra=1)
+    od = torch.tensor([0, 50000], dtype=torch.int64, device="cuda")
+    short = torch.empty(50000 // 128, device="cuda")
+    hs_lib.hs_power_normalize(hb.plan, spec, od, 0, 128, short, out, hb.ws)
+    with pytest.raises(hs_lib.HSError):
+        hb.sync_status()
+    with pytest.raises(hs_lib.HSError):
+        hs_lib.hs_power_normalize(hs.plan, spec, None, 50000, 100, med, out, hs.ws)  # block not allowed

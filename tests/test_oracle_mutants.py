@@ -59,6 +59,14 @@ MUTANTS = [
      "const int stage = 1;", ["test_pow2_stages_restrict_the_full_search"]),
     ("odd H are stages", "hs_oracle_body.h", "const int stage = !pow2 || (H & (H - 1)) == 0;",
      "const int stage = !pow2 || (H & 1) == 0 || H == 1;", ["test_pow2_stages_restrict_the_full_search"]),
+    ("upper median instead of lower", "hs_oracle.c", "m[j] = tmp[(size - 1) / 2];", "m[j] = tmp[size / 2];",
+     ["test_power_normalize_medians_are_lower_order_statistics"]),
+    ("interpolation against the wrong neighbour centre", "hs_oracle.c",
+     "float t = (d - hj) / ((float)block - hj + hn);", "float t = (d - hj) / ((float)block);",
+     ["test_power_normalize_interpolates_between_block_centres"]),
+    ("dereddening by the median, not the mean estimate", "hs_oracle.c",
+     "float x = base > 0.0f ? (P[k] * ln2) / base - 1.0f : 0.0f;", "float x = base > 0.0f ? P[k] / base - 1.0f : 0.0f;",
+     ["test_power_normalize_constant_and_zero", "test_power_normalize_whitens_red_noise"]),
     ("f16 ties round away from zero", "hs_oracle.c", "uint32_t h = (r + 0x0FFFu + ((r >> 13) & 1u)) >> 13;",
      "uint32_t h = (r + 0x1000u) >> 13;", ["test_standardize_cast_f16_matches_ieee_library"]),
     ("bf16 truncates", "hs_oracle.c", "return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);",
@@ -93,6 +101,7 @@ def _run_pin(name):
               "test_linearity": [("std",), ("fbin",)],
               "test_calibration_closed_form": [(v,) for v in pins.VARIANTS],
               "test_pow2_stages_restrict_the_full_search": [(v,) for v in pins.VARIANTS],
+              "test_power_normalize_medians_are_lower_order_statistics": [(1000, 128), (77, 128), (300, 256)],
               "test_adjoint_is_transpose_of_linear_map": [("std",), ("fbin",)]}
     for args in params.get(name, [()]):
         fn(*args)

@@ -566,3 +566,81 @@ def test_pow2_stages_restrict_the_full_search(variant):
     assert (p2["best_h"][~valid] == 0).all()
     if variant == "greedy":
         np.testing.assert_array_equal(p2["path"], full["path"])  # the recursion itself is unchanged
+
+
+# ---------------------------------------------------------------------------------------------
+# the step before the sums: power, block-median dereddening, standardisation
+# ---------------------------------------------------------------------------------------------
+
+def _cgauss(n, seed, scale=None):
+    rng = np.random.default_rng(seed)
+    z = (rng.standard_normal(n) + 1j * rng.standard_normal(n)) / np.sqrt(2.0)
+    return (z * (1.0 if scale is None else np.sqrt(scale))).astype(np.complex64)
+
+
+def _power32(z):
+    f = z.view(np.float32).reshape(-1, 2)
+    return f[:, 0] * f[:, 0] + f[:, 1] * f[:, 1]  # float32, each product and the sum rounded
+
+
+@pytest.mark.parametrize("n,block", [(1000, 128), (4096, 64), (77, 128), (1, 32), (300, 256)])
+def test_power_normalize_medians_are_lower_order_statistics(n, block):
+    z = _cgauss(n, 3 + n)
+    _, med = oracle.power_normalize(z, block)
+    P = _power32(z)
+    for j in range(med.size):
+        b = P[j * block:(j + 1) * block]
+        k = (b.size - 1) // 2
+        assert med[j] == np.partition(b, k)[k]
+
+
+def test_power_normalize_constant_and_zero():
+    z = np.full(1000, 2.0 + 0.0j, np.complex64)  # power exactly 4 everywhere
+    x, med = oracle.power_normalize(z, 128)
+    assert (med == 4.0).all()
+    assert (x == np.float32(0.693147180559945309417232) - np.float32(1.0)).all()
+    x0, _ = oracle.power_normalize(np.zeros(500, np.complex64), 64)
+    assert (x0 == 0.0).all()  # no power: no information
+
+
+def test_power_normalize_interpolates_between_block_centres():
+    """Blocks of constant power v_j: the baseline is the straight line through the points
+    (block centre, v_j), held flat before the first and after the last centre (numpy interp)."""
+    block, nblk = 64, 9
+    n = block * nblk - 23  # a partial last block
+    v = np.array([1.0, 3.0, 2.0, 8.0, 8.0, 0.5, 4.0, 2.5, 6.0])
+    amp = np.repeat(np.sqrt(v), block)[:n]
+    z = (amp + 0j).astype(np.complex64)
+    x, med = oracle.power_normalize(z, block)
+    P = _power32(z).astype(np.float64)
+    np.testing.assert_array_equal(med, P[::block])
+    sizes = np.minimum(block, n - np.arange(nblk) * block)
+    centres = np.arange(nblk) * block + (sizes - 1) / 2.0
+    base = np.interp(np.arange(n), centres, med.astype(np.float64))
+    np.testing.assert_allclose(x, P * math.log(2.0) / base - 1.0, rtol=2e-6, atol=2e-6)
+
+
+def test_power_normalize_whitens_red_noise():
+    """White exponential power comes out with mean ~0 and sigma ~1 (the median of B exponentials
+    estimates ln 2 of the mean), and the same noise times a smooth red trend comes out the same."""
+    n, block = 1 << 16, 128
+    k = np.arange(n)
+    trend = 1.0 + 200.0 / (1.0 + k / 50.0)
+    xw, _ = oracle.power_normalize(_cgauss(n, 12), block)
+    xr, _ = oracle.power_normalize(_cgauss(n, 12, trend), block)
+    for qw, qr in zip(np.array_split(xw[4 * block:], 4), np.array_split(xr[4 * block:], 4)):
+        assert abs(qw.mean()) < 0.05 and abs(qw.std() - 1.0) < 0.1
+        assert abs(qr.mean() - qw.mean()) < 0.01 and abs(qr.std() / qw.std() - 1.0) < 0.02
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_power_normalize_reduced_precision_is_the_rounded_fp32(dtype):
+    z = _cgauss(5000, 21)
+    x32, _ = oracle.power_normalize(z, 128)
+    xr, _ = oracle.power_normalize(z, 128, dtype)
+    if dtype == "f16":
+        np.testing.assert_array_equal(xr, x32.astype(np.float16).view(np.uint16))
+    else:
+        import torch
+
+        np.testing.assert_array_equal(xr, torch.from_numpy(x32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16))
