@@ -538,6 +538,19 @@ def main():
             del hp, op
             torch.cuda.empty_cache()
 
+        # the step after the sums: sift the sorted Eq. 1 candidate list of the batch (harmonics and
+        # neighbouring bins of stronger candidates dropped, k <= 8, 1.5 bins)
+        sift = None
+        if not args.no_secondary and "std" in variants:
+            so = torch.empty(cap * 16, dtype=torch.uint8, device="cuda")
+            so_count = torch.zeros(1, dtype=torch.int64, device="cuda")
+            sift_ms = _time_ms(torch, stream, lambda: hs.hs_sift_candidates(outs["std"]["cand"], outs["std"]["cand_count"],
+                                                                              so, so_count, cand_tmp, h.ws, stream=stream),
+                               2)
+            sift = {"variant": "std", "candidates_in": min(int(outs["std"]["cand_count"].item()), cap),
+                    "kept": int(so_count.item()), "ms": sift_ms, "kmax": 8, "tol_bins": 1.5}
+            del so, so_count
+
     value = world * total * HMAX / (step_ms / 1e3)
     peaks, peak_src = load_peaks()
     avg = {v: statistics.mean(per_variant[v]) for v in variants}
@@ -593,6 +606,8 @@ def main():
         line["eq1_staged_spans"] = staged
     if pow2:
         line["pow2_stages"] = pow2
+    if sift:
+        line["sift"] = sift
     if not args.no_secondary:
         del graphs, outs, xd
         torch.cuda.empty_cache()

@@ -266,6 +266,20 @@ hs_status hs_power_normalize(const hs_plan* plan, const float* d_spec, const int
 hs_status hs_sort_candidates(hs_candidate* d_cand, const unsigned long long* d_count, int64_t capacity,
                              hs_candidate* d_tmp, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Sift a sorted candidate list (the step after the sums): within each (variant, spectrum) group, drop
+ * every candidate to which a stronger candidate of the group is related.  A candidate's fundamental
+ * is (bin / H, z / H) for Eq. 1 and its 2-D form (they report the H-th harmonic) and (bin, z) for
+ * Eq. 2-4; two candidates are related when, for some k = 1..kmax, the higher fundamental lies within
+ * k*tol_bins bins and k*tol_z drift rows of k times the lower one (harmonics and neighbouring bins).
+ * Stronger: larger snr, or equal snr and earlier in the list.  Comparisons in FP32, each operation
+ * rounded.  d_cand: min(count, capacity) candidates sorted by hs_sort_candidates; the kept ones go
+ * to d_out, sorted the same way, and their number to d_out_count (set on the device).  d_out and
+ * d_tmp hold capacity candidates; the workspace is the sort's.  O(g^2) comparisons per group of g. */
+hs_status hs_sift_candidates(const hs_candidate* d_cand, const unsigned long long* d_count, int64_t capacity,
+                             float tol_bins, float tol_z, int kmax, hs_candidate* d_out,
+                             unsigned long long* d_out_count, hs_candidate* d_tmp, void* d_ws, size_t ws_bytes,
+                             cudaStream_t stream);
+
 /* ---- CUDA graphs -------------------------------------------------------------------------- */
 
 typedef struct hs_graph hs_graph; /* an instantiated CUDA graph plus the arguments it was built for */

@@ -250,6 +250,54 @@ def noise_calibration(variant, hmax: int = 32):
     return mu.astype(np.float32), (1.0 / sd).astype(np.float32)
 
 
+CANDIDATE_DTYPE = np.dtype([("spectrum", "<u4"), ("bin", "<u4"), ("snr", "<f4"), ("z", "<i2"), ("h", "u1"),
+                            ("variant", "u1")])
+
+
+def _fundamentals32(cand):
+    """(frequency, drift) of each candidate's fundamental in bins, FP32 arrays: Eq. 1 and its 2-D form
+    report the H-th harmonic (bin / H, z / H); Eq. 2-4 report the fundamental's own bin."""
+    h = np.maximum(cand["h"].astype(np.float32), np.float32(1))
+    b = cand["bin"].astype(np.float32)
+    z = cand["z"].astype(np.float32)
+    is_std = cand["variant"].astype(np.int64) == STD
+    f = np.where(is_std, (b / h).astype(np.float32), b).astype(np.float32)
+    fz = np.where(is_std, (z / h).astype(np.float32), z).astype(np.float32)
+    return f, fz
+
+
+def sift_candidates(cand, tol: float = 1.5, tol_z: float = 1.5, kmax: int = 8):
+    """Keep mask of a candidate list (structured CANDIDATE_DTYPE, in any order): a candidate is
+    dropped when a stronger candidate of the same variant and spectrum is related to it (larger snr,
+    or equal snr and earlier in the list).  Related: for some k = 1..kmax the higher fundamental lies
+    within k*tol bins and k*tol_z rows of k times the lower one; every operation in FP32 (numpy
+    float32 arrays, each elementwise operation rounded)."""
+    n = len(cand)
+    keep = np.ones(n, bool)
+    f, fz = _fundamentals32(cand)
+    snr = cand["snr"].astype(np.float32)
+    group = cand["variant"].astype(np.int64) << 32 | cand["spectrum"].astype(np.int64)
+    t, tz = np.float32(tol), np.float32(tol_z)
+    for i in range(n):
+        j = np.nonzero(group == group[i])[0]
+        j = j[j != i]
+        stronger = (snr[j] > snr[i]) | ((snr[j] == snr[i]) & (j < i))
+        j = j[stronger]
+        if j.size == 0:
+            continue
+        a_low = f[j] <= f[i]  # the other candidate is the lower one when its frequency is not higher
+        fl = np.where(a_low, f[j], f[i]).astype(np.float32)
+        zl = np.where(a_low, fz[j], fz[i]).astype(np.float32)
+        fh = np.where(a_low, f[i], f[j]).astype(np.float32)
+        zh = np.where(a_low, fz[i], fz[j]).astype(np.float32)
+        rel = np.zeros(j.size, bool)
+        for k in range(1, kmax + 1):
+            kf = np.float32(k)
+            rel |= (np.abs(fh - kf * fl) <= kf * t) & (np.abs(zh - kf * zl) <= kf * tz)
+        keep[i] = not rel.any()
+    return keep
+
+
 def candidates(best_snr, best_h, threshold: float, spectrum: int = 0):
     """The thresholded candidate set: every bin whose best snr is strictly above the threshold,
     as (spectrum, bin, snr, H) rows in bin order."""

@@ -76,6 +76,7 @@ def _load():
         "hs_backward": ([_P, I, _P, _P, I, I64, _P, _P, _P, _P, _P], I),
         "hs_standardize_cast": ([_P, _P, I, I64, _P, _P, I, _P, _P], I),
         "hs_power_normalize": ([_P, _P, _P, I, I64, I, _P, I64, _P, _P, SZ, _P], I),
+        "hs_sift_candidates": ([_P, _P, I64, ctypes.c_float, ctypes.c_float, I, _P, _P, _P, _P, SZ, _P], I),
         "hs_sort_candidates": ([_P, _P, I64, _P, _P, SZ, _P], I),
         "hs_graph_create_batched": ([_P, I, _P, _P, I, U32, _P, _P, SZ, _P, ctypes.POINTER(_P)], I),
         "hs_graph_launch": ([_P, _P], I),
@@ -226,6 +227,16 @@ def hs_power_normalize(plan, spec, offsets, n_bins, block, medians, out, ws, str
     return _check(_lib.hs_power_normalize(plan, _ptr(spec), _ptr(offsets), n_spectra, int(n_bins), int(block),
                                           _ptr(medians), medians.numel(), _ptr(out), _ptr(ws), ws.numel(),
                                           _stream(stream)), "hs_power_normalize")
+
+
+def hs_sift_candidates(cand, cand_count, out, out_count, tmp, ws, tol_bins=1.5, tol_z=1.5, kmax=8, stream=None):
+    """Drop every candidate of a sorted list to which a stronger candidate of its (variant, spectrum)
+    group is harmonically related or adjacent; the kept ones go to ``out`` (sorted), their number to
+    ``out_count``."""
+    cap = cand.numel() // 16
+    return _check(_lib.hs_sift_candidates(_ptr(cand), _ptr(cand_count), cap, float(tol_bins), float(tol_z), int(kmax),
+                                          _ptr(out), _ptr(out_count), _ptr(tmp), _ptr(ws), ws.numel(),
+                                          _stream(stream)), "hs_sift_candidates")
 
 
 def hs_graph_create_batched(plan, variant_mask, x, offsets, outs, ws, first_id=0, stream=None):

@@ -348,6 +348,20 @@ hs_status hs_sort_candidates(hs_candidate* d_cand, const unsigned long long* d_c
                                              stream));
 }
 
+hs_status hs_sift_candidates(const hs_candidate* d_cand, const unsigned long long* d_count, int64_t capacity,
+                             float tol_bins, float tol_z, int kmax, hs_candidate* d_out,
+                             unsigned long long* d_out_count, hs_candidate* d_tmp, void* d_ws, size_t ws_bytes,
+                             cudaStream_t stream) {
+    if (!d_cand || !d_count || !d_out || !d_out_count || !d_tmp || !d_ws || capacity < 0) return HS_ERR_INVALID;
+    if (!(tol_bins >= 0.f) || !(tol_z >= 0.f) || !std::isfinite(tol_bins) || !std::isfinite(tol_z) || kmax < 1 ||
+        kmax > 64 || d_out == d_cand)
+        return HS_ERR_INVALID;
+    if (!aligned(d_cand, 16) || !aligned(d_out, 16) || !aligned(d_tmp, 16) || !aligned(d_ws, 256)) return HS_ERR_ALIGN;
+    if (ws_bytes < sort_scratch_bytes(capacity)) return HS_ERR_NOMEM;
+    return check_cuda(launch_sift_candidates(d_cand, d_count, capacity, tol_bins, tol_z, kmax, d_out, d_out_count,
+                                             d_tmp, reinterpret_cast<WsControl*>(d_ws), stream));
+}
+
 struct hs_graph {
     cudaGraph_t graph;
     cudaGraphExec_t exec;

@@ -295,4 +295,142 @@ cudaError_t launch_sort_candidates(hs_candidate* cand, const unsigned long long*
     return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------------------------------
+// Candidate sifting.  In a list sorted by (variant, spectrum, z, bin), a candidate is dropped when a
+// stronger candidate of its (variant, spectrum) group is related to it: some k = 1..kmax puts the
+// higher fundamental within k*tol bins (and k*tol_z drift rows) of k times the lower one.  The
+// fundamental is (bin / H, z / H) for Eq. 1 and its 2-D form, which report the H-th harmonic, and
+// the bin itself for Eq. 2-4.  Stronger: larger snr, or equal snr and earlier in the list.  Every
+// comparison is taken in FP32 with each operation rounded, in the order written.
+// ------------------------------------------------------------------------------------------
+namespace {
+
+struct Fund {
+    float f, z, snr;
+    unsigned long long key;  // (variant, spectrum)
+};
+
+__device__ __forceinline__ Fund fundamental(const uint4 c) {
+    Fund r;
+    const float bin = (float)c.y;
+    const float z = (float)(int16_t)(c.w & 0xFFFFu);
+    const unsigned h = max((c.w >> 16) & 0xFFu, 1u), v = c.w >> 24;
+    if (v == (unsigned)HS_STD) {
+        r.f = __fdiv_rn(bin, (float)h);
+        r.z = __fdiv_rn(z, (float)h);
+    } else {
+        r.f = bin;
+        r.z = z;
+    }
+    r.snr = __uint_as_float(c.z);
+    r.key = ((unsigned long long)v << 32) | c.x;
+    return r;
+}
+
+__device__ __forceinline__ bool related_k(float fl, float zl, float fh, float zh, float tol, float tol_z, int k) {
+    const float kf = (float)k;
+    return fabsf(__fsub_rn(fh, __fmul_rn(kf, fl))) <= __fmul_rn(kf, tol) &&
+           fabsf(__fsub_rn(zh, __fmul_rn(kf, zl))) <= __fmul_rn(kf, tol_z);
+}
+
+// Whether some k = 1..kmax relates the two fundamentals.  Without drift, g(k) = |fh - k fl| - k tol
+// is convex in k with its kink at fh / fl, falling before it and, when fl > tol, rising after it; so
+// if any k <= kmax has g(k) <= 0, so does the integer minimiser of g over 1..kmax, which lies next to
+// fh / fl (clamped to 1..kmax).  The integers around it are tested, one further on each side for the
+// rounding of the quotient, each with the exact test.  With drift, or fl <= tol, every k is tested.
+__device__ __forceinline__ bool related(float4 a, float4 b, float tol, float tol_z, int kmax) {
+    const bool al = a.x <= b.x;
+    const float fl = al ? a.x : b.x, zl = al ? a.y : b.y, fh = al ? b.x : a.x, zh = al ? b.y : a.y;
+    int k0 = 1, k1 = kmax;
+    if (zl == 0.f && zh == 0.f && fl > tol) {
+        const float kc = __fdiv_rn(fh, fl);
+        const int kf = kc < (float)kmax ? (int)kc : kmax;  // floor of a non-negative quotient, capped
+        k0 = max(1, kf - 1);
+        k1 = min(kmax, kf + 2);
+    }
+    for (int k = k0; k <= k1; ++k)
+        if (related_k(fl, zl, fh, zh, tol, tol_z, k)) return true;
+    return false;
+}
+
+__device__ __forceinline__ unsigned long long cand_key(const uint4* c, uint32_t i) {
+    const uint4 v = c[i];
+    return ((unsigned long long)(v.w >> 24) << 32) | v.x;
+}
+
+__device__ __forceinline__ uint32_t sift_count(const unsigned long long* count, long long cap) {
+    const unsigned long long cnt = *count;
+    return (uint32_t)(cnt < (unsigned long long)cap ? cnt : (unsigned long long)cap);
+}
+
+// (fundamental frequency, drift, snr) of every candidate, once
+__global__ void __launch_bounds__(256) k_sift_fund(const uint4* cand, const unsigned long long* count, long long cap,
+                                                   float4* fund) {
+    const uint32_t n = sift_count(count, cap);
+    for (uint32_t i = blockIdx.x * 256u + threadIdx.x; i < n; i += gridDim.x * 256u) {
+        const Fund r = fundamental(cand[i]);
+        fund[i] = make_float4(r.f, r.z, r.snr, 0.f);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sift(const uint4* cand, const float4* fund, const unsigned long long* count,
+                                              long long cap, float tol, float tol_z, int kmax, uint4* out,
+                                              unsigned long long* out_count) {
+    const uint32_t n = sift_count(count, cap);
+    for (uint32_t base = blockIdx.x * 256u; base < n; base += gridDim.x * 256u) {
+        const uint32_t i = base + threadIdx.x;
+        bool keep = false;
+        uint4 ci = make_uint4(0u, 0u, 0u, 0u);
+        if (i < n) {
+            ci = cand[i];
+            const unsigned long long key = ((unsigned long long)(ci.w >> 24) << 32) | ci.x;
+            const float4 a = fund[i];
+            // the group [lo, end) of this (variant, spectrum) in the sorted list
+            uint32_t lo = 0, hi = i;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (cand_key(cand, mid) < key) lo = mid + 1; else hi = mid;
+            }
+            uint32_t end = i + 1, top = n;
+            while (end < top) {
+                const uint32_t mid = (end + top) >> 1;
+                if (cand_key(cand, mid) <= key) end = mid + 1; else top = mid;
+            }
+            keep = true;
+            for (uint32_t j = lo; j < end && keep; ++j) {
+                if (j == i) continue;
+                const float4 b = fund[j];
+                const bool stronger = b.z > a.z || (b.z == a.z && j < i);
+                if (stronger && related(b, a, tol, tol_z, kmax)) keep = false;
+            }
+        }
+        // warp-aggregated append of the kept candidates (unordered; sorted afterwards)
+        const unsigned mask = __ballot_sync(0xffffffffu, keep);
+        if (mask) {
+            const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+            unsigned long long pos = 0;
+            if (lane == leader) pos = atomicAdd(out_count, (unsigned long long)__popc(mask));
+            pos = __shfl_sync(0xffffffffu, pos, leader);
+            if (keep) out[pos + __popc(mask & ((1u << lane) - 1u))] = ci;
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sift_candidates(const hs_candidate* cand, const unsigned long long* count, int64_t capacity,
+                                   float tol, float tol_z, int kmax, hs_candidate* out,
+                                   unsigned long long* out_count, hs_candidate* tmp, WsControl* ctl,
+                                   cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out_count, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || capacity <= 0) return e;
+    const int nb = (int)std::min<int64_t>((capacity + 255) / 256, 4096);
+    float4* fund = reinterpret_cast<float4*>(tmp);  // scratch until the final sort
+    k_sift_fund<<<nb, 256, 0, s>>>(reinterpret_cast<const uint4*>(cand), count, capacity, fund);
+    k_sift<<<nb, 256, 0, s>>>(reinterpret_cast<const uint4*>(cand), fund, count, capacity, tol, tol_z, kmax,
+                              reinterpret_cast<uint4*>(out), out_count);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return launch_sort_candidates(out, out_count, capacity, tmp, ctl, s);
+}
+
 }  // namespace hs

@@ -125,6 +125,10 @@ cudaError_t launch_standardize_cast(const float* p, const int64_t* offsets, int 
 cudaError_t launch_power_normalize(const float* spec, const int64_t* offsets, int n_spectra, int64_t n_bins, int block,
                                    float* medians, long long med_cap, hs_dtype dt, void* out, int64_t max_bins,
                                    int sm_count, int64_t* prefix, WsControl* ctl, cudaStream_t s);
+cudaError_t launch_sift_candidates(const hs_candidate* cand, const unsigned long long* count, int64_t capacity,
+                                   float tol, float tol_z, int kmax, hs_candidate* out,
+                                   unsigned long long* out_count, hs_candidate* tmp, WsControl* ctl,
+                                   cudaStream_t s);
 cudaError_t launch_sort_candidates(hs_candidate* cand, const unsigned long long* count, int64_t capacity,
                                    hs_candidate* tmp, WsControl* ctl, cudaStream_t s);
 

@@ -619,3 +619,83 @@ def test_power_normalize_single_and_errors(hs_lib, torch):
         hb.sync_status()
     with pytest.raises(hs_lib.HSError):
         hs_lib.hs_power_normalize(hs.plan, spec, None, 50000, 100, med, out, hs.ws)  # block not allowed
+
+
+# ---- candidate sifting (the step after the sums) ----
+
+def _synthetic_candidates(seed, n_groups=24):
+    """A sorted candidate list with harmonic families, neighbouring bins, drifts and snr ties, drawn
+    from a seeded generator (independent of any harmonic-sum output)."""
+    rng = np.random.default_rng(seed)
+    rows = {}
+    for g in range(n_groups):
+        v = [1, 2, 4, 8][g % 4]
+        spec = 100 + g // 4
+        for _ in range(rng.integers(1, 4)):  # pulsar families
+            f0 = rng.uniform(40.0, 400.0)
+            z0 = int(rng.integers(-6, 7)) if v == 1 and g % 8 == 0 else 0
+            for k in range(1, int(rng.integers(2, 10))):
+                for dn in (0, 1):
+                    h = int(rng.integers(1, 33)) if v == 1 else int(rng.integers(1, 17))
+                    b = int(round((h if v == 1 else 1) * k * f0 + dn + rng.normal(0, 0.4)))
+                    z = (h * k * z0) if v == 1 else 0
+                    rows[(v, spec, z, b)] = (round(float(rng.uniform(6, 30)) * 2) / 2, h)
+        for _ in range(int(rng.integers(5, 30))):  # unrelated bins
+            b = int(rng.integers(0, 20000))
+            rows[(v, spec, 0, b)] = (round(float(rng.uniform(6, 12)) * 2) / 2, int(rng.integers(1, 33)))
+    keys = sorted(rows, key=lambda k: (k[0], k[1], k[2] + 32768, k[3]))
+    c = np.zeros(len(keys), oracle.CANDIDATE_DTYPE)
+    for i, (v, spec, z, b) in enumerate(keys):
+        snr, h = rows[(v, spec, z, b)]
+        c[i] = (spec, b, snr, z, h, v)
+    return c
+
+
+@pytest.mark.parametrize("kmax,tol", [(8, 1.5), (3, 0.6), (1, 2.0)])
+def test_sift_candidates_matches_oracle(hs_lib, torch, kmax, tol):
+    c = _synthetic_candidates(11 + kmax)
+    cap = c.size + 37
+    hs = hs_lib.HarmonicSum(variants=0xF, cand_capacity=cap)
+    cand = torch.zeros(cap * 16, dtype=torch.uint8, device="cuda")
+    cand[: c.size * 16] = torch.from_numpy(c.view(np.uint8).copy()).cuda()
+    count = torch.tensor([c.size], dtype=torch.int64, device="cuda")
+    out = torch.empty_like(cand)
+    out_count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tmp = torch.empty_like(cand)
+    hs_lib.hs_sift_candidates(cand, count, out, out_count, tmp, hs.ws, tol_bins=tol, tol_z=tol, kmax=kmax)
+    torch.cuda.synchronize()
+    keep = oracle.sift_candidates(c, tol=tol, tol_z=tol, kmax=kmax)
+    n = int(out_count.item())
+    got = out[: n * 16].cpu().numpy().view(oracle.CANDIDATE_DTYPE)
+    assert n == int(keep.sum()) and 0 < n < c.size
+    np.testing.assert_array_equal(got, c[keep])
+
+
+def test_sift_candidates_dense_families(hs_lib, torch):
+    """Many candidates per group with fundamentals spread over the whole k range, small ones near the
+    tolerance, exact multiples and near-misses: the narrowed search of the kernel must agree with the
+    oracle's loop over every k."""
+    rng = np.random.default_rng(3)
+    rows = {}
+    for g in range(6):
+        v = [4, 8, 2][g % 3]
+        f = np.concatenate([rng.uniform(0.5, 3.0, 40), rng.uniform(3, 60, 150),
+                            np.outer(rng.uniform(5, 40, 10), np.arange(1, 12)).ravel() + rng.normal(0, 0.8, 110)])
+        for x in f:
+            b = int(max(0, round(x)))
+            rows[(v, 7 + g, 0, b)] = (round(float(rng.uniform(6, 20)) * 4) / 4, 1)
+    keys = sorted(rows, key=lambda k: (k[0], k[1], k[2] + 32768, k[3]))
+    c = np.zeros(len(keys), oracle.CANDIDATE_DTYPE)
+    for i, (v, spec, z, b) in enumerate(keys):
+        c[i] = (spec, b, rows[(v, spec, z, b)][0], z, 1, v)
+    cap = c.size
+    hs = hs_lib.HarmonicSum(variants=0xF, cand_capacity=cap)
+    cand = torch.from_numpy(c.view(np.uint8).copy()).cuda()
+    count = torch.tensor([c.size], dtype=torch.int64, device="cuda")
+    out, tmp = torch.empty_like(cand), torch.empty_like(cand)
+    out_count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for kmax, tol in [(8, 1.5), (11, 0.7), (16, 2.5)]:
+        hs_lib.hs_sift_candidates(cand, count, out, out_count, tmp, hs.ws, tol_bins=tol, tol_z=tol, kmax=kmax)
+        keep = oracle.sift_candidates(c, tol=tol, tol_z=tol, kmax=kmax)
+        n = int(out_count.item())
+        np.testing.assert_array_equal(out[: n * 16].cpu().numpy().view(oracle.CANDIDATE_DTYPE), c[keep])

@@ -644,3 +644,44 @@ def test_power_normalize_reduced_precision_is_the_rounded_fp32(dtype):
         import torch
 
         np.testing.assert_array_equal(xr, torch.from_numpy(x32).to(torch.bfloat16).view(torch.int16).numpy().view(np.uint16))
+
+
+# ---------------------------------------------------------------------------------------------
+# candidate sifting: hand-built lists
+# ---------------------------------------------------------------------------------------------
+
+def _cands(rows):
+    c = np.zeros(len(rows), oracle.CANDIDATE_DTYPE)
+    for i, (spec, b, snr, z, h, v) in enumerate(rows):
+        c[i] = (spec, b, snr, z, h, v)
+    return c
+
+
+def test_sift_drops_harmonics_and_neighbours_of_stronger_candidates():
+    """Worked by hand (tol 1.5 bins, k <= 8): a candidate goes when any stronger one of its group is
+    related to it, whether or not that stronger one is itself kept."""
+    FB, STD = oracle.FBIN, oracle.STD
+    c = _cands([
+        (0, 100, 20.0, 0, 4, FB),   # 300 = 3 x 100 and 300 is stronger: dropped
+        (0, 200, 10.0, 0, 4, FB),   # 200 = 2 x 100 (stronger): dropped
+        (0, 101, 15.0, 0, 4, FB),   # |101 - 100| = 1 <= 1.5: dropped
+        (0, 137, 12.0, 0, 4, FB),   # 137 - 100, 137 - 101, 300 - 2 x 137 = 26 > 3: kept
+        (0, 300, 25.0, 0, 8, FB),   # the strongest of its group: kept
+        (0, 1000, 9.0, 0, 4, FB),   # 1000 = 5 x 200 (snr 10 > 9): dropped
+        (1, 200, 10.0, 0, 4, FB),   # another spectrum: kept
+        (0, 400, 30.0, 0, 8, STD),  # Eq. 1 reports the H-th harmonic: fundamental 400/8 = 50; kept
+        (0, 800, 29.0, 0, 16, STD), # fundamental 800/16 = 50 again, weaker: dropped
+    ])
+    keep = oracle.sift_candidates(c, tol=1.5, tol_z=1.5, kmax=8)
+    np.testing.assert_array_equal(keep, [False, False, False, True, True, False, True, True, False])
+    # with k <= 4 the fifth harmonic no longer counts
+    assert oracle.sift_candidates(c, tol=1.5, tol_z=1.5, kmax=4)[5]
+
+
+def test_sift_ties_keep_the_earlier_and_drift_counts():
+    FB, STD = oracle.FBIN, oracle.STD
+    c = _cands([(3, 500, 8.0, 0, 2, FB), (3, 501, 8.0, 0, 2, FB), (3, 1000, 8.0, 0, 2, FB)])
+    np.testing.assert_array_equal(oracle.sift_candidates(c), [True, False, False])
+    # 2-D candidates (Eq. 1 form): the same frequency but a different drift is not the same signal
+    d = _cands([(0, 640, 12.0, 40, 4, STD), (0, 640, 11.0, -40, 4, STD), (0, 1280, 10.0, 80, 8, STD)])
+    np.testing.assert_array_equal(oracle.sift_candidates(d, tol=1.5, tol_z=1.5), [True, True, False])
