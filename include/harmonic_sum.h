@@ -80,6 +80,11 @@ typedef enum hs_dtype { HS_F32 = 0, HS_F16 = 1, HS_BF16 = 2 } hs_dtype;
  * bin; Eq. 2-4 still add every harmonic to their running sums.  The every-H table reads -inf for
  * H that are not stages. */
 #define HS_FLAG_POW2_STAGES 8
+/* Eq. 4 with its first term fixed: h_1 = x(n) and the pairwise choice starts at harmonic 2 with j = 0
+ * (the form with h_1 = x(n) and the first pair at 2n), instead of max(x(n), x(n+1)) as written.  H is
+ * valid while H (n + 1) <= N (the furthest read is H n + H - 1).  Forward sums and adjoint;
+ * calibrate with hs_noise_calibration_flags. */
+#define HS_FLAG_GREEDY_FIXED1 16
 
 typedef struct hs_plan hs_plan; /* opaque; host memory only */
 
@@ -150,8 +155,9 @@ hs_status hs_plan_set_calibration(hs_plan* plan, hs_variant v, const float* mu, 
 hs_status hs_noise_calibration(hs_variant v, int hmax, float* mu, float* isig);
 
 /* The same for the sums a plan with these flags computes: with HS_FLAG_MAX_WINDOW0, Eq. 2 windows
- * hold i + 1 bins, so Hn(i+1) and k <= i+1 replace Hn(i) and k <= i above.  flags = 0 gives
- * hs_noise_calibration. */
+ * hold i + 1 bins, so Hn(i+1) and k <= i+1 replace Hn(i) and k <= i above; with
+ * HS_FLAG_GREEDY_FIXED1, Eq. 4 has mu_H = (H - 1) / (2 sqrt(H)), sigma_H^2 = (1 + 5/4 (H - 1)) / H.
+ * flags = 0 gives hs_noise_calibration. */
 hs_status hs_noise_calibration_flags(hs_variant v, int hmax, int flags, float* mu, float* isig);
 
 /* Bytes of device workspace a call needs for up to n_spectra spectra (1 for hs_sum_1d / 2-D).

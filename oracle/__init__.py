@@ -16,11 +16,12 @@ import subprocess
 
 import numpy as np
 
-STD, MAX, FBIN, GREEDY, MAX0 = 1, 2, 4, 8, 16
+STD, MAX, FBIN, GREEDY, MAX0, GREEDY1 = 1, 2, 4, 8, 16, 32
 POW2 = 64  # flag bit: search only H = 1, 2, 4, .. (pass pow2=True)
 # "max0": Eq. 2 with the window j = 0..i (bins i*n .. i*n+i), a variant flag; "max" is the window as
 # written, j = 1..i
-VARIANTS = {"std": STD, "max": MAX, "fbin": FBIN, "greedy": GREEDY, "max0": MAX0}
+# "greedy1": Eq. 4 with the first term fixed at x(n) and the first pair at 2n, a variant flag
+VARIANTS = {"std": STD, "max": MAX, "fbin": FBIN, "greedy": GREEDY, "max0": MAX0, "greedy1": GREEDY1}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRCS = [os.path.join(_HERE, "hs_oracle.c"), os.path.join(_HERE, "hs_oracle_body.h")]
@@ -108,7 +109,7 @@ def hs_1d(variant, x, hmax: int = 32, mu=None, isig=None, fp64: bool = False, po
     mu, isig = _tables(mu, isig, hmax, dt)
     best = np.empty(N, dt)
     bh = np.empty(N, np.uint8)
-    path = np.zeros(N, np.uint32) if v & ~POW2 == GREEDY else None
+    path = np.zeros(N, np.uint32) if v & ~POW2 in (GREEDY, GREEDY1) else None
     ah = np.empty((hmax, N), dt) if all_h else None
     fn = _load().hs_oracle_1d_f64 if fp64 else _load().hs_oracle_1d_f32
     fn(v, _ptr(x), N, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh), _ptr(path), _ptr(ah), _threads(nthreads))
@@ -149,7 +150,7 @@ def hs_batched(variant, x, offsets, hmax: int = 32, mu=None, isig=None, fp64: bo
     mu, isig = _tables(mu, isig, hmax, dt)
     best = np.empty(total, dt)
     bh = np.empty(total, np.uint8)
-    path = np.zeros(total, np.uint32) if v & ~POW2 == GREEDY else None
+    path = np.zeros(total, np.uint32) if v & ~POW2 in (GREEDY, GREEDY1) else None
     fn = _load().hs_oracle_batched_f64 if fp64 else _load().hs_oracle_batched_f32
     fn(v, _ptr(x[base:base + total]), _ptr(offs), len(offs) - 1, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh),
        _ptr(path), _threads(nthreads))

@@ -13,6 +13,7 @@
  * all lie in [0, N):
  *     Eq. 1 (STD)            always hmax (every index is <= n)
  *     Eq. 2, 4 (MAX, MAX0, GREEDY) H*(n+1) <= N-1   (the furthest read is H*n+H)
+ *     GREEDY1                    H*(n+1) <= N     (the furthest read is H*n+H-1: j <= H-2)
  *     Eq. 3 (FBIN)           H*n <= N-1        (n = 0 reads x(0) for every H)
  * A bin with no valid H gets snr = -inf and H = 0.
  */
@@ -29,6 +30,7 @@
 #define HS_O_FBIN 4
 #define HS_O_GREEDY 8
 #define HS_O_MAX0 16 /* Eq. 2 with the window j = 0..i (a variant flag; the paper writes j = 1..i) */
+#define HS_O_GREEDY1 32 /* Eq. 4 with the first term fixed at x(n) and the first pair at 2n (a variant flag) */
 #define HS_O_POW2 64 /* flag bit OR'ed into a variant: only H = 1, 2, 4, .. are stages of the search */
 #define HS_O_HMAX 32
 
@@ -39,6 +41,9 @@ int hs_oracle_hvalid(int variant, int64_t n, int64_t N, int hmax) {
     if (variant == HS_O_FBIN) {
         if (n == 0) return N >= 1 ? hmax : 0;
         lim = (N - 1) / n; /* H*n <= N-1 */
+    } else if (variant == HS_O_GREEDY1) {
+        lim = N / (n + 1); /* H*(n+1) <= N */
+        if (N < 1) lim = 0;
     } else {
         lim = (N - 1) / (n + 1); /* H*(n+1) <= N-1 */
         if (N < 1) lim = 0;
@@ -98,6 +103,8 @@ void hs_oracle_grad_f64(int variant, const double* x, int64_t N, int hmax, const
                 m = base + j0;
                 for (int jj = j0 + 1; jj <= i; ++jj)
                     if (x[base + jj] > x[m]) m = base + jj;
+            } else if (variant == HS_O_GREEDY1 && i == 1) {
+                m = n; /* the fixed first term */
             } else {
                 int64_t base = (int64_t)i * n + j;
                 if (x[base + 1] > x[base]) {
@@ -230,6 +237,8 @@ void hs_oracle_power_normalize(const float* spec, int64_t n, int block, int dtyp
  *        disjoint for n >= H, since (i+1) n > i n + i).
  *   GREEDY: each step is the max of two fresh iid Exp(1) bins: mean 1/2, variance 5/4, so
  *        mu_H = sqrt(H)/2, sigma_H = sqrt(5/4).
+ *   GREEDY1: the first term is one standardised bin (0, 1), the H - 1 others as above, so
+ *        mu_H = (H - 1) / (2 sqrt(H)), sigma_H^2 = (1 + 5/4 (H - 1)) / H.
  * mu[0], sigma[0] are set to (0, 1).
  */
 void hs_oracle_noise_moments(int variant, int hmax, double* mu, double* sigma) {
@@ -252,6 +261,9 @@ void hs_oracle_noise_moments(int variant, int hmax, double* mu, double* sigma) {
         } else if (variant == HS_O_GREEDY) {
             mu[H] = 0.5 * sqrt((double)H);
             sigma[H] = sqrt(1.25);
+        } else if (variant == HS_O_GREEDY1) {
+            mu[H] = 0.5 * (H - 1) / sqrt((double)H);
+            sigma[H] = sqrt((1.0 + 1.25 * (H - 1)) / H);
         } else {
             mu[H] = 0.0;
             sigma[H] = 1.0;

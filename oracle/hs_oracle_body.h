@@ -10,6 +10,7 @@
  *   Eq. 3  bins i*n.
  *   Eq. 4  start with S = 0, j = 0; harmonic i compares x(i*n+j) (left) with x(i*n+j+1) (right);
  *          the right bin is taken only when strictly larger, and then j grows by one.
+ *          Variant flag GREEDY1: the first term is x(n) and the pairs start at harmonic 2 (j = 0).
  *   Terms are summed in the order i = 1..H; h = S * c_H with c_H = 1/sqrt(H);
  *   snr = (h - mu_H) * isig_H; the best H is the first H with the largest snr.
  *   Variant flag POW2 (the stages of SIGPROC/PRESTO-style searches): only H = 1, 2, 4, 8, .. are
@@ -56,7 +57,11 @@ static void FN(hs_bin_)(int variant, const REAL* x, int64_t N, int64_t n, int hm
                 /* Eq. 3 */
                 S = S + x[(int64_t)H * n];
                 sum = S;
-            } else { /* HS_O_GREEDY, Eq. 4 */
+            } else if (variant == HS_O_GREEDY1 && H == 1) {
+                /* Eq. 4 variant flag: the first term is x(n) itself; pairs start at harmonic 2 */
+                S = S + x[n];
+                sum = S;
+            } else { /* HS_O_GREEDY, Eq. 4 (and GREEDY1 from H = 2 on) */
                 int64_t base = (int64_t)H * n + j;
                 REAL l = x[base], r = x[base + 1], t;
                 if (r > l) {

@@ -53,7 +53,7 @@ struct Bin<HS_STD, T> {
     template <bool P2>
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
-                                                uint32_t& path, uint32_t j0) {
+                                                uint32_t& path, uint32_t flags) {
         float S[kHmax + 1];
 #pragma unroll
         for (int H = 0; H <= kHmax; ++H) S[H] = 0.f;
@@ -134,8 +134,9 @@ struct Bin<HS_MAX, T> {
     template <bool P2>
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
-                                                uint32_t& path, uint32_t j0) {
+                                                uint32_t& path, uint32_t flags) {
         const int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
+        const uint32_t j0 = (flags & HS_FLAG_MAX_WINDOW0) ? 0u : 1u;
         float S = 0.f;
         for (int i = 1; i <= hv; ++i) {
             const uint32_t base = (uint32_t)i * n;
@@ -156,7 +157,7 @@ struct Bin<HS_FBIN, T> {
     template <bool P2>
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
-                                                uint32_t& path, uint32_t j0) {
+                                                uint32_t& path, uint32_t flags) {
         const int hv = (n == 0) ? hmax : (int)min((uint32_t)hmax, (N - 1) / n);
         float S = 0.f;
         for (int i0 = 1; i0 <= hv; i0 += 4) {
@@ -180,23 +181,29 @@ struct Bin<HS_FBIN, T> {
 };
 
 // Eq. 4: harmonic i compares x(i*n+j) with x(i*n+j+1); the right bin wins only if strictly larger,
-// and then j grows by one.
+// and then j grows by one.  Under HS_FLAG_GREEDY_FIXED1 the first term is x(n) itself and the pairs
+// start at harmonic 2; the furthest read is then H*n+H-1, so H is valid while H*(n+1) <= N.
 template <typename T>
 struct Bin<HS_GREEDY, T> {
     template <bool P2>
     static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
-                                                uint32_t& path, uint32_t j0) {
-        const int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
+                                                uint32_t& path, uint32_t flags) {
+        const bool fixed1 = (flags & HS_FLAG_GREEDY_FIXED1) != 0;
+        const int hv = N >= 1 ? (int)min((uint32_t)hmax, (fixed1 ? N : N - 1) / (n + 1)) : 0;
         float S = 0.f;
         uint32_t j = 0, p = 0;
         for (int i = 1; i <= hv; ++i) {
-            const uint32_t b = (uint32_t)i * n + j;
-            const float l = ldx(x, b), r = ldx(x, b + 1);
-            const bool right = r > l;
-            p |= (right ? 1u : 0u) << (i - 1);
-            j += right ? 1u : 0u;
-            S = __fadd_rn(S, right ? r : l);
+            if (fixed1 && i == 1) {
+                S = __fadd_rn(S, ldx(x, n));
+            } else {
+                const uint32_t b = (uint32_t)i * n + j;
+                const float l = ldx(x, b), r = ldx(x, b + 1);
+                const bool right = r > l;
+                p |= (right ? 1u : 0u) << (i - 1);
+                j += right ? 1u : 0u;
+                S = __fadd_rn(S, right ? r : l);
+            }
             const bool stage = !P2 || is_pow2(i);
             const float snr = stage ? calibrate(tb, S, i) : -INFINITY;
             if (stage) keep_best(snr, i, best, bh);
@@ -241,8 +248,7 @@ __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, ui
         int bh = 0;
         uint32_t path = 0;
         if (active) {
-            Bin<V, T>::template eval<P2>(x, N, n, w.hmax, tb, o.all_h, N, best, bh, path,
-                            (w.flags & HS_FLAG_MAX_WINDOW0) ? 0u : 1u);
+            Bin<V, T>::template eval<P2>(x, N, n, w.hmax, tb, o.all_h, N, best, bh, path, (uint32_t)w.flags);
             o.best_snr[out_off + n] = best;
             o.best_h[out_off + n] = (uint8_t)bh;
             if (V == HS_GREEDY && o.path) o.path[out_off + n] = path;

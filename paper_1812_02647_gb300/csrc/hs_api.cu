@@ -18,7 +18,8 @@ using namespace hs;
 
 namespace {
 
-constexpr int kPlanFlags = HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS | HS_FLAG_MAX_WINDOW0 | HS_FLAG_POW2_STAGES;
+constexpr int kPlanFlags = HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS | HS_FLAG_MAX_WINDOW0 | HS_FLAG_POW2_STAGES |
+                           HS_FLAG_GREEDY_FIXED1;
 
 bool single_variant(int v) { return v == HS_STD || v == HS_MAX || v == HS_FBIN || v == HS_GREEDY; }
 
@@ -172,6 +173,9 @@ hs_status hs_noise_calibration_flags(hs_variant v, int hmax, int flags, float* m
             var_sum += hn2;
             m = mean_sum / std::sqrt((double)H);
             sd = std::sqrt(var_sum / H);
+        } else if (v == HS_GREEDY && (flags & HS_FLAG_GREEDY_FIXED1)) {
+            m = 0.5 * (H - 1) / std::sqrt((double)H);  // one bin, then H - 1 maxima of two
+            sd = std::sqrt((1.0 + 1.25 * (H - 1)) / H);
         } else if (v == HS_GREEDY) {
             m = 0.5 * std::sqrt((double)H);  // max of two unit exponentials: mean 3/2, variance 5/4
             sd = std::sqrt(1.25);

@@ -43,7 +43,7 @@ def test_status_strings(hs_lib):
 @pytest.mark.parametrize("bad", [dict(variants=0), dict(variants=16), dict(hmax=0), dict(hmax=33),
                                  dict(dtype=3), dict(max_bins=-1), dict(max_bins=(1 << 26) + 1),
                                  dict(nz=5, z_min=1, hmax=16), dict(nz=5, z_min=-5, hmax=16),
-                                 dict(nz=5, z_min=-2, hmax=17), dict(cand_capacity=-1), dict(flags=16),
+                                 dict(nz=5, z_min=-2, hmax=17), dict(cand_capacity=-1), dict(flags=32),
                                  dict(nz=5, z_min=-2, hmax=16, flags=8),
                                  dict(threshold=float("nan"))])
 def test_plan_create_rejects(hs_lib, bad):
@@ -99,6 +99,10 @@ def test_library_noise_calibration_matches_oracle(hs_lib):
     # Eq. 2 with the window j = 0..i
     mu, isig = hs_lib.hs_noise_calibration("max", 32, flags=hs_lib.FLAG_MAX_WINDOW0)
     omu, oisig = oracle.noise_calibration("max0", 32)
+    np.testing.assert_array_equal(mu, omu)
+    np.testing.assert_array_equal(isig, oisig)
+    mu, isig = hs_lib.hs_noise_calibration("greedy", 32, flags=hs_lib.FLAG_GREEDY_FIXED1)
+    omu, oisig = oracle.noise_calibration("greedy1", 32)
     np.testing.assert_array_equal(mu, omu)
     np.testing.assert_array_equal(isig, oisig)
     with pytest.raises(hs_lib.HSError):

@@ -699,3 +699,52 @@ def test_sift_candidates_dense_families(hs_lib, torch):
         keep = oracle.sift_candidates(c, tol=tol, tol_z=tol, kmax=kmax)
         n = int(out_count.item())
         np.testing.assert_array_equal(out[: n * 16].cpu().numpy().view(oracle.CANDIDATE_DTYPE), c[keep])
+
+
+# ---- Eq. 4 with the first term fixed at x(n) (HS_FLAG_GREEDY_FIXED1), against the oracle's "greedy1" ----
+
+def _greedy1(hs_lib, dtype=0, max_spectra=1, flags=0):
+    mu, isig = oracle.noise_calibration("greedy1", 32)
+    hs = hs_lib.HarmonicSum(variants=hs_lib.GREEDY, dtype=dtype, max_bins=1 << 22, threshold=THR,
+                            cand_capacity=1 << 16, flags=flags | hs_lib.FLAG_GREEDY_FIXED1, max_spectra=max_spectra)
+    hs.set_calibration("greedy", mu, isig)
+    return hs, mu, isig
+
+
+@pytest.mark.parametrize("n_bins", [1, 2, 3, 33, 1000, 65536 + 13, 300001])
+@pytest.mark.parametrize("dtype", ["f32", "f16", "bf16"])
+def test_greedy_fixed1_bit_exact(hs_lib, torch, n_bins, dtype):
+    x = hs_synth.spectrum(78, 0, n_bins)
+    xd, xw = _widen(torch, x, dtype)
+    hs, mu, isig = _greedy1(hs_lib, dtype={"f32": 0, "f16": 1, "bf16": 2}[dtype], flags=hs_lib.FLAG_OUT_ALL_H)
+    o = hs.sum_1d("greedy", xd, all_h=True)
+    r = oracle.hs_1d("greedy1", xw, hmax=32, mu=mu, isig=isig, all_h=True, nthreads=8)
+    np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    np.testing.assert_array_equal(o["path"].cpu().numpy().view(np.uint32), r["path"])
+    _check_candidates(hs_lib, o, r["best_snr"], r["best_h"])
+
+
+def test_greedy_fixed1_batched_and_adjoint(hs_lib, torch):
+    lens = [0, 8, 4096, 100000, 12, 250000]
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    x = hs_synth.batch(96, offsets)
+    hs, mu, isig = _greedy1(hs_lib, max_spectra=len(lens))
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda()
+    o = hs.sum_batched("greedy", xd, od, first_id=5)
+    assert hs.sync_status() == hs_lib.OK
+    r = oracle.hs_batched("greedy1", x, offsets, mu=mu, isig=isig, nthreads=8)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    np.testing.assert_array_equal(o["path"].cpu().numpy().view(np.uint32), r["path"])
+    _check_candidates(hs_lib, o, r["best_snr"], r["best_h"], offsets, first_id=5)
+    g = torch.sigmoid(o["best_snr"] - 5.0)
+    grad = hs.backward("greedy", xd, g, o["best_h"], o["path"], od).cpu().numpy().astype(np.float64)
+    gn = g.cpu().numpy().astype(np.float64)
+    exp = np.zeros(x.size)
+    for s in range(len(lens)):
+        a, b = offsets[s], offsets[s + 1]
+        exp[a:b] = oracle.grad_1d("greedy1", x[a:b], gn[a:b], r["best_h"][a:b], isig=isig.astype(np.float64))
+    np.testing.assert_allclose(grad, exp, rtol=1e-5, atol=1e-6)

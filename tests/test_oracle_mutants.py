@@ -67,6 +67,10 @@ MUTANTS = [
     ("dereddening by the median, not the mean estimate", "hs_oracle.c",
      "float x = base > 0.0f ? (P[k] * ln2) / base - 1.0f : 0.0f;", "float x = base > 0.0f ? P[k] / base - 1.0f : 0.0f;",
      ["test_power_normalize_constant_and_zero", "test_power_normalize_whitens_red_noise"]),
+    ("greedy1 pairs from the first harmonic", "hs_oracle_body.h", "} else if (variant == HS_O_GREEDY1 && H == 1) {",
+     "} else if (variant == HS_O_GREEDY1 && H == 0) {", ["test_h1_identity", "test_greedy_bruteforce_paths"]),
+    ("greedy1 range as for greedy", "hs_oracle.c", "lim = N / (n + 1); /* H*(n+1) <= N */",
+     "lim = (N - 1) / (n + 1);", ["test_range_limits"]),
     ("f16 ties round away from zero", "hs_oracle.c", "uint32_t h = (r + 0x0FFFu + ((r >> 13) & 1u)) >> 13;",
      "uint32_t h = (r + 0x1000u) >> 13;", ["test_standardize_cast_f16_matches_ieee_library"]),
     ("bf16 truncates", "hs_oracle.c", "return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);",
@@ -95,6 +99,7 @@ def _run_pin(name):
     fn = getattr(pins, name)
     params = {"test_h1_identity": [(v,) for v in pins.VARIANTS],
               "test_max_bruteforce": [("max",), ("max0",)],
+              "test_greedy_bruteforce_paths": [("greedy",), ("greedy1",)],
               "test_delta_spike_max": [("max",), ("max0",)],
               "test_constant_spectrum": [(v, c) for v in pins.VARIANTS for c in (1.0, 3.5)],
               "test_range_limits": [(v,) for v in pins.VARIANTS],

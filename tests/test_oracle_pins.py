@@ -16,7 +16,9 @@ import hs_synth
 import oracle
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-VARIANTS = ["std", "max", "fbin", "greedy", "max0"]  # max0: Eq. 2 with the window j = 0..i (variant flag)
+# max0: Eq. 2 with the window j = 0..i; greedy1: Eq. 4 with the first term fixed at x(n) (variant flags)
+VARIANTS = ["std", "max", "fbin", "greedy", "max0", "greedy1"]
+GREEDY = ("greedy", "greedy1")
 
 
 def j0(variant):
@@ -75,6 +77,8 @@ def test_h1_identity(variant):
         expect = np.append(x[1:], -np.inf)  # x(n+1); the last bin has no valid H
     elif variant == "max0":
         expect = np.append(np.maximum(x[:-1], x[1:]), -np.inf)  # max(x(n), x(n+1))
+    elif variant == "greedy1":
+        expect = x  # x(n) itself, valid at every bin
     else:
         expect = np.append(np.maximum(x[:-1], x[1:]), -np.inf)
     np.testing.assert_array_equal(row, expect.astype(np.float32))
@@ -97,7 +101,7 @@ def test_constant_spectrum(variant, c):
         if hv:
             # positive c: the largest valid H wins; negative c: H = 1 wins
             assert r["best_h"][n] == (hv if c > 0 else 1)
-    if variant == "greedy":
+    if variant in GREEDY:
         assert not r["path"].any()  # ties keep the left bin
 
 
@@ -134,6 +138,8 @@ def test_range_limits(variant):
         elif variant == "fbin":
             assert hv == (hmax if n == 0 else min(hmax, (N - 1) // n))
             assert hv * n <= N - 1 and (hv == hmax or (hv + 1) * n > N - 1)
+        elif variant == "greedy1":  # the furthest read is H n + H - 1
+            assert hv * (n + 1) <= N and (hv == hmax or (hv + 1) * (n + 1) > N)
         else:
             assert hv * (n + 1) <= N - 1 and (hv == hmax or (hv + 1) * (n + 1) > N - 1)
     r = oracle.hs_1d(variant, rand_spectrum(N, 3), hmax=hmax)
@@ -260,21 +266,25 @@ def test_max_bruteforce(variant):
                 assert r64["all_h"][H - 1, n] == pytest.approx(s64 / math.sqrt(H), rel=1e-14, abs=1e-14)
 
 
-def test_greedy_bruteforce_paths():
+@pytest.mark.parametrize("variant", GREEDY)
+def test_greedy_bruteforce_paths(variant):
     """Enumerate every left/right choice sequence; exactly one obeys the step rule, and it is the
-    oracle's path and sum."""
+    oracle's path and sum (greedy1: the first term is x(n), its bit never set)."""
+    first = 2 if variant == "greedy1" else 1
     for seed in range(6):
         N = 64
         x = rand_spectrum(N, 600 + seed).astype(np.float64)
         x[10] = x[11]  # plant a tie: the rule keeps the left bin
-        r = oracle.hs_1d("greedy", x, hmax=6, fp64=True, all_h=True)
+        r = oracle.hs_1d(variant, x, hmax=6, fp64=True, all_h=True)
         for n in range(N):
-            hv = oracle.hvalid("greedy", n, N, 6)
+            hv = oracle.hvalid(variant, n, N, 6)
             for H in range(1, hv + 1):
                 obeying = []
                 for bits in range(1 << H):
-                    j, ok, s = 0, True, 0.0
-                    for i in range(1, H + 1):
+                    if first == 2 and bits & 1:
+                        continue
+                    j, ok, s = 0, True, (x[n] if first == 2 else 0.0)
+                    for i in range(first, H + 1):
                         right = (bits >> (i - 1)) & 1
                         l, rr = x[i * n + j], x[i * n + j + 1]
                         if right != (1 if rr > l else 0):
@@ -338,6 +348,10 @@ def test_noise_calibration_tables():
     assert sd[2] == pytest.approx(math.sqrt(2.25 / 2), rel=1e-15)
     mu, sd = oracle.noise_moments("greedy", 32)
     assert mu[16] == pytest.approx(2.0) and sd[7] == pytest.approx(math.sqrt(1.25))
+    # first term one standardised bin, then four maxima of two: mean 4/2, variance 1 + 4 x 5/4
+    mu, sd = oracle.noise_moments("greedy1", 32)
+    assert mu[1] == 0.0 and sd[1] == 1.0
+    assert mu[5] == pytest.approx(2.0 / math.sqrt(5.0), rel=1e-15) and sd[5] == pytest.approx(math.sqrt(6.0 / 5.0))
     # windows of i + 1 bins: H = 1 is the max of two Exp(1) (mean 3/2, variance 5/4), H = 2 adds the
     # max of three (mean 11/6, variance 1 + 1/4 + 1/9)
     mu, sd = oracle.noise_moments("max0", 32)
@@ -362,7 +376,7 @@ def _abs_term_sum(variant, x64, hmax, r64):
     acc = np.zeros(N)
     j = np.zeros(N, np.int64)
     for H in range(1, hmax + 1):
-        ok = H * (n + 1) <= N - 1
+        ok = H * (n + 1) <= (N if variant == "greedy1" else N - 1)
         if variant in ("max", "max0"):
             w = np.stack([x64[np.minimum(H * n + k, N - 1)] for k in range(j0(variant), H + 1)])
             t = np.abs(w.max(axis=0))
@@ -391,7 +405,7 @@ def test_fp32_within_bound_of_fp64(variant):
     bound = 1e-5 * (np.abs(a64) + isig[1:hmax + 1, None].astype(np.float64) / np.sqrt(H) * tsum)
     err = np.abs(a32 - a64)
     assert (err[ok] <= bound[ok]).all()
-    if variant == "greedy":
+    if variant in GREEDY:
         np.testing.assert_array_equal(r32["path"], r64["path"])  # compares only, same in both modes
 
 
@@ -434,7 +448,7 @@ def _routing(variant, x, hmax):
     """Everything that decides which bins a bin's best sum reads."""
     r = oracle.hs_1d(variant, x, hmax=hmax, fp64=True, all_h=True)
     key = [r["best_h"].astype(np.int64)]
-    if variant == "greedy":
+    if variant in GREEDY:
         key.append(r["path"].astype(np.int64))
     if variant in ("max", "max0"):
         N = x.shape[0]
@@ -564,7 +578,7 @@ def test_pow2_stages_restrict_the_full_search(variant):
     np.testing.assert_array_equal(p2["best_h"][valid], np.array(stages)[k[valid]])
     np.testing.assert_array_equal(p2["best_snr"][valid], sub[k[valid], np.nonzero(valid)[0]])
     assert (p2["best_h"][~valid] == 0).all()
-    if variant == "greedy":
+    if variant in GREEDY:
         np.testing.assert_array_equal(p2["path"], full["path"])  # the recursion itself is unchanged
 
 
