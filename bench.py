@@ -358,10 +358,17 @@ def secondary(torch, hs, stream, tiles=None, reps=2):
                        cand_capacity=1 << 24)
     o = h.sum_2d(plane, stream=stream)
     per_plane = _time_ms(torch, stream, lambda: (o["cand_count"].zero_(), h.sum_2d(plane, out=o, stream=stream)), reps)
+    hf = hs.HarmonicSum(variants=hs.FBIN, hmax=16, nz=nz, z_min=z_min, max_bins=n_b, threshold=THR,
+                        cand_capacity=1 << 24)
+    of = hf.sum_2d(plane, stream=stream, variant="fbin")
+    per_plane_fbin = _time_ms(torch, stream, lambda: (of["cand_count"].zero_(),
+                                                      hf.sum_2d(plane, out=of, stream=stream, variant="fbin")), reps)
     out["fdas_2d"] = {"workload": "16 planes x 201 rows x 2^21 bins FP32, H = 1..16 (timed per plane, same plane)",
                       "ms_per_plane": per_plane, "ms_per_16_planes": per_plane * planes,
                       "cells_per_s": nz * n_b / (per_plane / 1e3),
-                      "harmonic_summed_cells_per_s": nz * n_b * 16 / (per_plane / 1e3)}
+                      "harmonic_summed_cells_per_s": nz * n_b * 16 / (per_plane / 1e3),
+                      "fbin_ms_per_plane": per_plane_fbin}
+    del hf, of
     del plane, o, h
     torch.cuda.empty_cache()
     return out

@@ -224,6 +224,14 @@ hs_status hs_sum_batched_noalloc(const hs_plan* plan, hs_variant v, const void* 
 hs_status hs_sum_2d(const hs_plan* plan, const void* d_plane, int64_t n_bins, int64_t row_stride,
                     uint32_t plane_id, const hs_out2d* out, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
+/* The same plane with a chosen variant: HS_STD is hs_sum_2d; HS_FBIN is the 2-D form of Eq. 3, in
+ * which the cell (n, z) is the fundamental and harmonic i reads x(i n, i z), summed in the order
+ * i = 1..H, with H valid while H n <= n_bins - 1 (every H at n = 0) and H z within the plane's
+ * rows.  Eq. 2 and 4 have no 2-D form in the paper: HS_ERR_UNSUPPORTED.  The plan must include v. */
+hs_status hs_sum_2d_variant(const hs_plan* plan, hs_variant v, const void* d_plane, int64_t n_bins,
+                            int64_t row_stride, uint32_t plane_id, const hs_out2d* out, void* d_ws, size_t ws_bytes,
+                            cudaStream_t stream);
+
 /* ---- adjoint ---------------------------------------------------------------------------- */
 
 /* Adjoint of best_snr with respect to x, with each bin's best H held fixed (the routing of the

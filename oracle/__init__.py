@@ -58,6 +58,7 @@ def _load():
             getattr(lib, "hs_oracle_2d_cells_" + sfx).argtypes = [P, I, I, I64, I64, I, P, P, P, P, I64, P, P]
             getattr(lib, "hs_oracle_batched_" + sfx).argtypes = [I, P, P, I, I, P, P, P, P, P, I]
             getattr(lib, "hs_oracle_2d_" + sfx).argtypes = [P, I, I, I64, I64, I, P, P, P, P, P, P, P, P, I]
+            getattr(lib, "hs_oracle_2d_fbin_" + sfx).argtypes = [P, I, I, I64, I64, I, P, P, P, P, P, P, P, P, I]
         lib.hs_oracle_grad_f64.argtypes = [I, P, I64, I, P, P, P, P]
         lib.hs_oracle_standardize_cast.argtypes = [P, I64, ctypes.c_float, ctypes.c_float, I, P]
         lib.hs_oracle_noise_moments.argtypes = [I, I, P, P]
@@ -161,8 +162,9 @@ def hs_batched(variant, x, offsets, hmax: int = 32, mu=None, isig=None, fp64: bo
 
 
 def hs_2d(plane, z_min: int, hmax: int = 16, mu=None, isig=None, fp64: bool = False, all_h: bool = False,
-          nthreads: int | None = None):
-    """2-D Eq. 1 over a (nz, n_bins) plane whose row r holds z = z_min + r."""
+          nthreads: int | None = None, variant: str = "std"):
+    """2-D Eq. 1 (variant "std") or its freq-bin form ("fbin": harmonic i at (i n, i z)) over a
+    (nz, n_bins) plane whose row r holds z = z_min + r."""
     dt = np.float64 if fp64 else np.float32
     plane = np.ascontiguousarray(plane, dtype=dt)
     nz, nb = plane.shape
@@ -173,7 +175,12 @@ def hs_2d(plane, z_min: int, hmax: int = 16, mu=None, isig=None, fp64: bool = Fa
     bhn = np.empty(nb, np.uint8)
     bzn = np.empty(nb, np.int32)
     ah = np.empty((hmax, nz, nb), dt) if all_h else None
-    fn = _load().hs_oracle_2d_f64 if fp64 else _load().hs_oracle_2d_f32
+    if variant == "std":
+        fn = _load().hs_oracle_2d_f64 if fp64 else _load().hs_oracle_2d_f32
+    elif variant == "fbin":
+        fn = _load().hs_oracle_2d_fbin_f64 if fp64 else _load().hs_oracle_2d_fbin_f32
+    else:
+        raise ValueError("2-D sums are defined for std and fbin")
     fn(_ptr(plane), nz, z_min, nb, nb, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh), _ptr(bn), _ptr(bhn),
        _ptr(bzn), _ptr(ah), _threads(nthreads))
     out = {"best_snr": best, "best_h": bh, "best_snr_n": bn, "best_h_n": bhn, "best_z_n": bzn}

@@ -190,6 +190,67 @@ void FN(hs_oracle_2d_)(const REAL* plane, int nz, int z_min, int64_t n_bins, int
 }
 
 /* Only the listed cells (row rows[k], bin bins[k]) of a 2-D plane, same definition as above. */
+/*
+ * 2-D form of Eq. 3 (a variant of the 2-D sums): the output cell (n, z) is the fundamental and
+ * harmonic i reads x(i*n, i*z), added in the order i = 1..H as a running sum.  H is valid while
+ * H*n <= N-1 (every H at n = 0) and H*z stays within the plane's rows.
+ */
+void FN(hs_oracle_2d_fbin_)(const REAL* plane, int nz, int z_min, int64_t n_bins, int64_t row_stride, int hmax,
+                            const REAL* mu_in, const REAL* isig_in, REAL* best_snr, uint8_t* best_h, REAL* best_snr_n,
+                            uint8_t* best_h_n, int32_t* best_z_n, REAL* all_h, int nthreads) {
+    REAL cs[HS_O_HMAX + 1], mu[HS_O_HMAX + 1], isig[HS_O_HMAX + 1];
+    for (int H = 0; H <= hmax; ++H) {
+        cs[H] = (H == 0) ? (REAL)0 : (REAL)(1.0 / sqrt((double)H));
+        mu[H] = mu_in ? mu_in[H] : (REAL)0;
+        isig[H] = isig_in ? isig_in[H] : (REAL)1;
+    }
+    const int64_t z_max = (int64_t)z_min + nz - 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) if (nthreads > 1)
+    for (int r = 0; r < nz; ++r) {
+        int64_t z = (int64_t)z_min + r;
+        for (int64_t n = 0; n < n_bins; ++n) {
+            REAL best = -INFINITY, S = 0;
+            int bh = 0;
+            for (int H = 1; H <= hmax; ++H) {
+                REAL snr = -INFINITY;
+                int valid = (H * n <= n_bins - 1) && (H * z >= z_min) && (H * z <= z_max);
+                if (valid) {
+                    S = S + plane[(H * z - z_min) * row_stride + H * n];
+                    REAL h = S * cs[H];
+                    snr = (h - mu[H]) * isig[H];
+                    if (snr > best) {
+                        best = snr;
+                        bh = H;
+                    }
+                }
+                if (all_h) all_h[((int64_t)(H - 1) * nz + r) * n_bins + n] = snr;
+                if (!valid) { /* later H are invalid too: reads move further out */
+                    for (int H2 = H + 1; H2 <= hmax; ++H2)
+                        if (all_h) all_h[((int64_t)(H2 - 1) * nz + r) * n_bins + n] = -INFINITY;
+                    break;
+                }
+            }
+            best_snr[(int64_t)r * n_bins + n] = best;
+            best_h[(int64_t)r * n_bins + n] = (uint8_t)bh;
+        }
+    }
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1) if (nthreads > 1)
+    for (int64_t n = 0; n < n_bins; ++n) {
+        REAL best = -INFINITY;
+        int br = 0;
+        for (int r = 0; r < nz; ++r) {
+            REAL v = best_snr[(int64_t)r * n_bins + n];
+            if (v > best) {
+                best = v;
+                br = r;
+            }
+        }
+        best_snr_n[n] = best;
+        best_h_n[n] = best_h[(int64_t)br * n_bins + n];
+        best_z_n[n] = z_min + br;
+    }
+}
+
 void FN(hs_oracle_2d_cells_)(const REAL* plane, int nz, int z_min, int64_t n_bins, int64_t row_stride, int hmax,
                              const REAL* mu_in, const REAL* isig_in, const int32_t* rows, const int64_t* bins,
                              int64_t count, REAL* best_snr, uint8_t* best_h) {

@@ -74,6 +74,7 @@ def _load():
         "hs_sum_1d": ([_P, I, _P, I64, U32, ctypes.POINTER(Out), _P, SZ, _P], I),
         "hs_sum_batched": ([_P, I, _P, _P, I, U32, ctypes.POINTER(Out), _P, SZ, _P], I),
         "hs_sum_2d": ([_P, _P, I64, I64, U32, ctypes.POINTER(Out2d), _P, SZ, _P], I),
+        "hs_sum_2d_variant": ([_P, I, _P, I64, I64, U32, ctypes.POINTER(Out2d), _P, SZ, _P], I),
         "hs_backward": ([_P, I, _P, _P, I, I64, _P, _P, _P, _P, _P], I),
         "hs_standardize_cast": ([_P, _P, I, I64, _P, _P, I, _P, _P], I),
         "hs_power_normalize": ([_P, _P, _P, I, I64, I, _P, I64, _P, _P, SZ, _P], I),
@@ -193,10 +194,14 @@ def hs_sum_batched(plan, variant, x, offsets, out: Out, ws, first_id=0, stream=N
                                       ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)), "hs_sum_batched")
 
 
-def hs_sum_2d(plan, plane, out: Out2d, ws, plane_id=0, stream=None):
+def hs_sum_2d(plan, plane, out: Out2d, ws, plane_id=0, stream=None, variant="std"):
+    """2-D sums over a (nz, n_bins) plane: Eq. 1 ("std") or its freq-bin form ("fbin")."""
     nz, nb = plane.shape
-    return _check(_lib.hs_sum_2d(plan, _ptr(plane), nb, plane.stride(0), plane_id, ctypes.byref(out), _ptr(ws),
-                                 ws.numel(), _stream(stream)), "hs_sum_2d")
+    if _variant(variant) == STD:
+        return _check(_lib.hs_sum_2d(plan, _ptr(plane), nb, plane.stride(0), plane_id, ctypes.byref(out), _ptr(ws),
+                                     ws.numel(), _stream(stream)), "hs_sum_2d")
+    return _check(_lib.hs_sum_2d_variant(plan, _variant(variant), _ptr(plane), nb, plane.stride(0), plane_id,
+                                         ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)), "hs_sum_2d_variant")
 
 
 def hs_backward(plan, variant, x, offsets, grad_snr, best_h, path, grad_x, stream=None):
@@ -365,7 +370,7 @@ class HarmonicSum:
         hs_sum_batched(self.plan, variant, x, offsets, self.out_struct(o), self.ws, first_id, stream)
         return o
 
-    def sum_2d(self, plane, plane_id=0, out=None, stream=None):
+    def sum_2d(self, plane, plane_id=0, out=None, stream=None, variant="std"):
         import torch
 
         nz, nb = plane.shape
@@ -382,7 +387,7 @@ class HarmonicSum:
                   o["best_h_n"].data_ptr(), o["best_z_n"].data_ptr(),
                   o["cand"].data_ptr() if "cand" in o else None,
                   o["cand_count"].data_ptr() if "cand_count" in o else None)
-        hs_sum_2d(self.plan, plane, s, self.ws, plane_id, stream)
+        hs_sum_2d(self.plan, plane, s, self.ws, plane_id, stream, variant=variant)
         return o
 
     def backward(self, variant, x, grad_snr, best_h, path=None, offsets=None, grad_x=None, stream=None):

@@ -254,9 +254,80 @@ __global__ void __launch_bounds__(k2dGroups * 32, 2) k_hs2d_pairs(const __grid_c
     }
 }
 
-cudaError_t launch_2d(const Tables& tab, const Work2d& w, const hs_out2d& o, long long cand_cap, WsControl* ctl,
-                      cudaStream_t s) {
+// ------------------------------------------------------------------------------------------
+// 2-D form of Eq. 3: the cell (n, z) is the fundamental and harmonic i reads x(i*n, i*z), added as a
+// running sum in the order i = 1..H.  H is valid while H*n <= N-1 (every H at n = 0) and H*z stays
+// within the plane's rows.  Same CTA layout and per-bin reduction as k_hs2d.
+// ------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(k2dBins * k2dGroups) k_hs2d_fbin(const __grid_constant__ Tables tb, const Work2d w,
+                                                                  const hs_out2d o, long long cand_cap, WsControl* ctl) {
+    __shared__ float s_snr[k2dGroups][k2dBins];
+    __shared__ int s_row[k2dGroups][k2dBins];
+    __shared__ int s_h[k2dGroups][k2dBins];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const uint32_t n = blockIdx.x * k2dBins + lane;
+    const uint32_t N = (uint32_t)w.n_bins;
+    const bool active = n < N;
+    const int z_max = w.z_min + w.nz - 1;
+    float rbest = -INFINITY;
+    int rrow = 0, rh = 0;
+    for (int r = g; r < w.nz; r += k2dGroups) {
+        const int z = w.z_min + r;
+        float best = -INFINITY;
+        int bh = 0;
+        if (active) {
+            int hv = w.hmax;
+            if (n > 0) hv = min(hv, (int)((N - 1) / n));
+            if (z > 0) hv = min(hv, z_max / z);
+            if (z < 0) hv = min(hv, w.z_min / z);  // both negative: the quotient floors towards zero
+            float S = 0.f;
+            for (int i = 1; i <= hv; ++i) {
+                S = __fadd_rn(S, __ldg(w.plane + (int64_t)(i * z - w.z_min) * w.row_stride + (int64_t)i * n));
+                keep_best(calibrate(tb, S, i), i, best, bh);
+            }
+            const size_t cell = (size_t)r * (size_t)w.n_bins + n;
+            o.best_snr[cell] = best;
+            o.best_h[cell] = (uint8_t)bh;
+            if (best > rbest) {  // rows visited in increasing order: the lowest row keeps ties
+                rbest = best;
+                rrow = r;
+                rh = bh;
+            }
+        }
+        if (o.cand)
+            append_candidate(active && best > w.threshold, o.cand, o.cand_count, cand_cap, &ctl->status, w.plane_id,
+                             n, best, z, bh, HS_FBIN);
+    }
+    s_snr[g][lane] = rbest;
+    s_row[g][lane] = rbest == -INFINITY ? 0x7fffffff : rrow;
+    s_h[g][lane] = rh;
+    __syncthreads();
+    if (g == 0 && active) {
+        float b = s_snr[0][lane];
+        int br = s_row[0][lane], bhh = s_h[0][lane];
+        for (int k = 1; k < k2dGroups; ++k) {
+            const float v = s_snr[k][lane];
+            const int rr = s_row[k][lane];
+            if (v > b || (v == b && rr < br)) {
+                b = v;
+                br = rr;
+                bhh = s_h[k][lane];
+            }
+        }
+        o.best_snr_n[n] = b;
+        o.best_h_n[n] = (uint8_t)bhh;
+        o.best_z_n[n] = (int16_t)(w.z_min + (br == 0x7fffffff ? 0 : br));
+    }
+}
+
+cudaError_t launch_2d(hs_variant v, const Tables& tab, const Work2d& w, const hs_out2d& o, long long cand_cap,
+                      WsControl* ctl, cudaStream_t s) {
     if (w.n_bins == 0) return cudaSuccess;
+    if (v == HS_FBIN) {
+        const unsigned grid = (unsigned)((w.n_bins + k2dBins - 1) / k2dBins);
+        k_hs2d_fbin<<<grid, k2dBins * k2dGroups, 0, s>>>(tab, w, o, cand_cap, ctl);
+        return cudaGetLastError();
+    }
     // float2 stores of the cell pair (n, n+1) need an even row length and an 8-byte aligned output
     const bool cells_aligned = (w.n_bins % 2) == 0 && (reinterpret_cast<uintptr_t>(o.best_snr) & 7) == 0;
     const bool small_plane = (uint64_t)w.nz * (uint64_t)w.row_stride < (1ull << 32);

@@ -266,7 +266,13 @@ hs_status hs_sum_batched(const hs_plan* p, hs_variant v, const void* d_x, const 
 
 hs_status hs_sum_2d(const hs_plan* p, const void* d_plane, int64_t n_bins, int64_t row_stride, uint32_t plane_id,
                     const hs_out2d* out, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
-    if (!p || p->d.nz <= 0 || !(p->d.variants & HS_STD)) return HS_ERR_INVALID;
+    return hs_sum_2d_variant(p, HS_STD, d_plane, n_bins, row_stride, plane_id, out, d_ws, ws_bytes, stream);
+}
+
+hs_status hs_sum_2d_variant(const hs_plan* p, hs_variant v, const void* d_plane, int64_t n_bins, int64_t row_stride,
+                            uint32_t plane_id, const hs_out2d* out, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
+    if (v == HS_MAX || v == HS_GREEDY) return HS_ERR_UNSUPPORTED;
+    if (!p || p->d.nz <= 0 || (v != HS_STD && v != HS_FBIN) || !(p->d.variants & v)) return HS_ERR_INVALID;
     if (p->d.dtype != HS_F32) return HS_ERR_UNSUPPORTED;
     if (!d_plane || n_bins < 0 || n_bins > p->d.max_bins || row_stride < n_bins) return HS_ERR_INVALID;
     if (!aligned(d_plane, 16) || (row_stride * 4) % 16 != 0) return HS_ERR_ALIGN;
@@ -285,7 +291,8 @@ hs_status hs_sum_2d(const hs_plan* p, const void* d_plane, int64_t n_bins, int64
     w.hmax = p->d.hmax;
     w.plane_id = plane_id;
     w.threshold = p->d.threshold;
-    return check_cuda(launch_2d(p->tab[0], w, *out, p->d.cand_capacity, reinterpret_cast<WsControl*>(d_ws), stream));
+    return check_cuda(launch_2d(v, p->tab[vindex(v)], w, *out, p->d.cand_capacity, reinterpret_cast<WsControl*>(d_ws),
+                                stream));
 }
 
 hs_status hs_backward(const hs_plan* p, hs_variant v, const void* d_x, const int64_t* d_offsets, int n_spectra,

@@ -111,8 +111,8 @@ struct Work2d {
     uint32_t plane_id;
     float threshold;
 };
-cudaError_t launch_2d(const Tables& tab, const Work2d& w, const hs_out2d& o, long long cand_cap, WsControl* ctl,
-                      cudaStream_t s);
+cudaError_t launch_2d(hs_variant v, const Tables& tab, const Work2d& w, const hs_out2d& o, long long cand_cap,
+                      WsControl* ctl, cudaStream_t s);
 
 // adjoint (hs_adjoint.cu)
 cudaError_t launch_backward(hs_variant v, hs_dtype dt, const Tables& tab, const void* x, const int64_t* offsets,

@@ -748,3 +748,30 @@ def test_greedy_fixed1_batched_and_adjoint(hs_lib, torch):
         a, b = offsets[s], offsets[s + 1]
         exp[a:b] = oracle.grad_1d("greedy1", x[a:b], gn[a:b], r["best_h"][a:b], isig=isig.astype(np.float64))
     np.testing.assert_allclose(grad, exp, rtol=1e-5, atol=1e-6)
+
+
+# ---- 2-D freq-bin form ----
+
+@pytest.mark.parametrize("nz,z_min,nb", [(11, -5, 3001), (7, -3, 4096), (1, 0, 1000)])
+def test_2d_fbin_bit_exact(hs_lib, torch, nz, z_min, nb):
+    stride = (nb + 3) // 4 * 4
+    full = np.stack([hs_synth.spectrum(123, r, stride) for r in range(nz)]).astype(np.float32)
+    plane = torch.from_numpy(full).cuda()[:, :nb]
+    hs = hs_lib.HarmonicSum(variants=hs_lib.STD | hs_lib.FBIN, hmax=16, nz=nz, z_min=z_min, max_bins=stride,
+                            threshold=THR, cand_capacity=1 << 16)
+    o = hs.sum_2d(plane, plane_id=4, variant="fbin")
+    r = oracle.hs_2d(full[:, :nb], z_min, hmax=16, variant="fbin", nthreads=8)
+    for k in ("best_snr", "best_h", "best_snr_n", "best_h_n"):
+        np.testing.assert_array_equal(o[k].cpu().numpy(), r[k], err_msg=k)
+    np.testing.assert_array_equal(o["best_z_n"].cpu().numpy().astype(np.int32), r["best_z_n"])
+    c = hs_lib.read_candidates(o)
+    exp = np.nonzero(r["best_snr"].ravel() > THR)[0]
+    assert c.size == exp.size and (c["variant"] == hs_lib.FBIN).all() and (c["spectrum"] == 4).all()
+    got = np.sort((c["z"].astype(np.int64) - z_min) * nb + c["bin"].astype(np.int64))
+    np.testing.assert_array_equal(got, exp)
+    s = hs_lib.Out2d(o["best_snr"].data_ptr(), o["best_h"].data_ptr(), o["best_snr_n"].data_ptr(),
+                     o["best_h_n"].data_ptr(), o["best_z_n"].data_ptr(), None, None)
+    for v in ("max", "greedy"):  # no 2-D form in the paper
+        with pytest.raises(hs_lib.HSError) as e:
+            hs_lib.hs_sum_2d(hs.plan, plane, s, hs.ws, variant=v)
+        assert e.value.status == hs_lib.ERR_UNSUPPORTED

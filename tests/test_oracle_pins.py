@@ -699,3 +699,45 @@ def test_sift_ties_keep_the_earlier_and_drift_counts():
     # 2-D candidates (Eq. 1 form): the same frequency but a different drift is not the same signal
     d = _cands([(0, 640, 12.0, 40, 4, STD), (0, 640, 11.0, -40, 4, STD), (0, 1280, 10.0, 80, 8, STD)])
     np.testing.assert_array_equal(oracle.sift_candidates(d, tol=1.5, tol_z=1.5), [True, True, False])
+
+
+# ---------------------------------------------------------------------------------------------
+# 2-D freq-bin form: harmonic i of the cell (n, z) at (i n, i z)
+# ---------------------------------------------------------------------------------------------
+
+def test_2d_fbin_zero_row_is_1d_fbin_and_ranges():
+    nz, z_min, nb = 9, -4, 300
+    plane = np.stack([rand_spectrum(nb, 70 + r) for r in range(nz)])
+    r2 = oracle.hs_2d(plane, z_min, hmax=16, fp64=True, all_h=True, variant="fbin")
+    r1 = oracle.hs_1d("fbin", plane[-z_min], hmax=16, fp64=True, all_h=True)
+    np.testing.assert_array_equal(r2["all_h"][:, -z_min, :], r1["all_h"])
+    # row z: valid H need H*z within [-4, 4] (and H*n <= nb - 1)
+    for r in range(nz):
+        z = z_min + r
+        hz = 16 if z == 0 else (4 // abs(z))
+        for n in (0, 1, 7, 150, 299):
+            hn = 16 if n == 0 else min(16, (nb - 1) // n)
+            hv = min(hz, hn)
+            col = r2["all_h"][:, r, n]
+            assert np.isfinite(col[:hv]).all() and np.isneginf(col[hv:]).all(), (z, n, hv)
+
+
+def test_2d_fbin_delta_spike_and_constant():
+    nz, z_min, nb, A = 13, -6, 200, 2.0
+    n0, z0 = 120, -6
+    plane = np.zeros((nz, nb))
+    plane[z0 - z_min, n0] = A
+    r = oracle.hs_2d(plane, z_min, hmax=16, fp64=True, all_h=True, variant="fbin")
+    for rr in range(nz):
+        z = z_min + rr
+        for n in range(1, nb):
+            for H in range(1, 17):
+                v = r["all_h"][H - 1, rr, n]
+                if not np.isfinite(v):
+                    continue
+                hit = any(i * n == n0 and i * z == z0 for i in range(1, H + 1))
+                assert v == pytest.approx(A * hit / math.sqrt(H), abs=1e-15), (z, n, H)
+    c = oracle.hs_2d(np.full((nz, nb), 1.5), z_min, hmax=16, fp64=True, all_h=True, variant="fbin")["all_h"]
+    for H in range(1, 17):
+        v = c[H - 1][np.isfinite(c[H - 1])]
+        np.testing.assert_allclose(v, 1.5 * math.sqrt(H), rtol=1e-14)
