@@ -775,3 +775,27 @@ def test_2d_fbin_bit_exact(hs_lib, torch, nz, z_min, nb):
         with pytest.raises(hs_lib.HSError) as e:
             hs_lib.hs_sum_2d(hs.plan, plane, s, hs.ws, variant=v)
         assert e.value.status == hs_lib.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("variant,flag,ovariant", [("max", "FLAG_MAX_WINDOW0", "max0"),
+                                                   ("greedy", "FLAG_GREEDY_FIXED1", "greedy1"),
+                                                   ("std", None, "std")])
+def test_flags_combined_with_pow2_stages(hs_lib, torch, variant, flag, ovariant):
+    """A variant flag together with the power-of-two stage search, single spectrum and batch."""
+    x = hs_synth.spectrum(79, 0, 70001)
+    flags = hs_lib.FLAG_POW2_STAGES | (getattr(hs_lib, flag) if flag else 0)
+    mu, isig = oracle.noise_calibration(ovariant, 32)
+    hs = hs_lib.HarmonicSum(variants=hs_lib.VARIANTS[variant], threshold=THR, cand_capacity=1 << 16,
+                            flags=flags | hs_lib.FLAG_OUT_ALL_H, max_spectra=2)
+    hs.set_calibration(variant, mu, isig)
+    xd = torch.from_numpy(x).cuda()
+    o = hs.sum_1d(variant, xd, all_h=True)
+    r = oracle.hs_1d(ovariant, x, hmax=32, mu=mu, isig=isig, all_h=True, pow2=True, nthreads=8)
+    np.testing.assert_array_equal(o["all_h"].cpu().numpy(), r["all_h"])
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    offsets = np.array([0, 30000, 70000], np.int64)
+    ob = hs.sum_batched(variant, xd, torch.from_numpy(offsets).cuda())
+    rb = oracle.hs_batched(ovariant, x, offsets, mu=mu, isig=isig, pow2=True, nthreads=8)
+    np.testing.assert_array_equal(ob["best_snr"].cpu().numpy()[:70000], rb["best_snr"])
+    np.testing.assert_array_equal(ob["best_h"].cpu().numpy()[:70000], rb["best_h"])
