@@ -576,10 +576,12 @@ def main():
         gbs = compulsory_bytes(v) / (avg[v] / 1e3) / 1e9
         per_roof[v] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
     traffic = None
+    binding = None
     try:
         tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         if tj.get("csrc_sha16") == csrc_sha16() and dom == "std" and not args.staged_spans:
             traffic = tj["dram_bytes_per_bin"] * total
+            binding = tj.get("ncu_pct")
     except Exception:
         pass
     if dom == "std":
@@ -589,6 +591,8 @@ def main():
         roof = {"bound": "alu", "kernel": kname, "achieved": tf, "peak": alu_peak,
                 "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock", "unit": "TFLOP/s",
                 "frac": tf / alu_peak, "traffic": traffic, "algorithmic_flops_per_launch": 528.0 * total}
+        if binding:  # what binds the kernel (ncu, same sources): L1 load wavefronts and issue
+            roof["ncu_pct_of_peak"] = binding
     else:
         r = per_roof[dom]
         roof = {**r, "kernel": "hs::k_hs1d_batched<%s>" % dom, "peak_source": peak_src, "traffic": None,
