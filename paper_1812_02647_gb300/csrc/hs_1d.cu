@@ -18,7 +18,16 @@ struct Bin;
 
 // hmax = 32, outputs n and n+1 together.  For fraction f <= 1 their bins differ by 0 or 1: with
 // W = n*F + 2^31, bin(n) = W >> 32 and bin(n+1) = (W + F) >> 32, which is one more exactly when
-// the low word of W carries on adding F.  Both candidates are loaded and the carry picks one.
+// the low word of W carries on adding F.  Both candidates are loaded and the carry picks one.  The
+// low word of W is lo + 2^31 (lo = low word of n*F), and an unsigned compare of lo + 2^31 is a signed
+// compare of lo itself, so the carry test needs no add.
+// (lo + 2^31 mod 2^32) >u ~F  <=>  (int)lo > (int)(~F ^ 2^31): flipping the top bit maps unsigned
+// order onto signed order.
+template <uint32_t F>
+struct CarryBound {
+    static constexpr int32_t value = (int32_t)(~F ^ 0x80000000u);
+};
+
 template <typename T, int K, bool P2>
 __device__ __forceinline__ void farey_pair_step(const T* x, uint32_t n, float2 (&S)[kHmax + 1]) {
     constexpr Frac f = farey_at(K);
@@ -35,7 +44,7 @@ __device__ __forceinline__ void farey_pair_step(const T* x, uint32_t n, float2 (
         const T* p = x + k;
         const float a = widen<T>(__ldg(p)), b = widen<T>(__ldg(p + 1));
         v.x = a;
-        v.y = (lo + 0x80000000u > 0xFFFFFFFFu - F) ? b : a;
+        v.y = ((int32_t)lo > CarryBound<F>::value) ? b : a;
     }
 #pragma unroll
     for (int m = 1; m * f.q <= kHmax; ++m)

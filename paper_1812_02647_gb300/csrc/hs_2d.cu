@@ -137,40 +137,45 @@ constexpr int k2dPairBins = 64;  // bins per CTA on the fast path (32 lanes x 2)
 
 
 
-// floor((2*z*p + q) / (2*q)) for any sign of z (round half up of z*p/q)
+// The row of fraction p/q at drift z, round-half-up(z*p/q) = floor((2zp + q) / (2q)) for any sign of z,
+// in unsigned arithmetic: with a = 2zp + 65537q (= 2zp + q + 2q*32768, positive for |z| <= 32767 and
+// below 2^21), floor(a / 2q) = umulhi(a, ceil(2^32 / 2q)) exactly (the error a / 2^32 stays below
+// 1/(2q)), and the row is that minus 32768.  Its element offset in the plane is
+// umulhi(...) * stride + base, base = -(32768 + z_min) * stride (the plane holds fewer than 2^32
+// elements, so the offset is exact modulo 2^32).
 template <int P, int Q>
-__device__ __forceinline__ int zround_frac(int z) {
-    const int a = 2 * z * P + Q;
-    return a >= 0 ? a / (2 * Q) : -((-a + 2 * Q - 1) / (2 * Q));
+__device__ __forceinline__ uint32_t row_offset16(int z, uint32_t stride, uint32_t base) {
+    constexpr uint32_t R = (uint32_t)(((1ull << 32) + 2 * Q - 1) / (2 * Q));
+    const uint32_t a = (uint32_t)(z * (2 * P) + 65537 * Q);
+    return __umulhi(a, R) * stride + base;
 }
 
+// n even and n+1 < row length, so both reads of every fraction stay inside the row (k(n) + 1 <= n + 1).
 template <int K>
-__device__ __forceinline__ void farey16_pair_step(const float* plane, uint32_t stride, int z, int z_min, uint32_t n,
-                                                  uint32_t nmax, float2 (&S)[HS_HMAX_2D + 1]) {
+__device__ __forceinline__ void farey16_pair_step(const float* plane, int z, uint32_t stride, uint32_t base, uint32_t n,
+                                                  float2 (&S)[HS_HMAX_2D + 1]) {
     constexpr Frac16 f = farey16_at(K);
-    // element offset of the row round(z*p/q) (the plane holds fewer than 2^32 elements)
-    const uint32_t roff = (uint32_t)(zround_frac<f.p, f.q>(z) - z_min) * stride;
+    const uint32_t roff = row_offset16<f.p, f.q>(z, stride, base);
     float2 v;
     if (f.q == 1) {
         v.x = __ldg(plane + (roff + n));
-        v.y = __ldg(plane + (roff + min(n + 1u, nmax)));
+        v.y = __ldg(plane + (roff + n + 1));
     } else {
         constexpr uint32_t F = (uint32_t)((((uint64_t)f.p << 32) + f.q - 1) / f.q);
         const uint32_t lo = n * F;
         const uint32_t k = __umulhi(n, F) + (lo >> 31);
-        const float a = __ldg(plane + (roff + k)), b = __ldg(plane + (roff + min(k + 1u, nmax)));
+        const float a = __ldg(plane + (roff + k)), b = __ldg(plane + (roff + k + 1));
         v.x = a;
-        v.y = (lo + 0x80000000u > 0xFFFFFFFFu - F) ? b : a;
+        v.y = ((int32_t)lo > (int32_t)(~F ^ 0x80000000u)) ? b : a;  // (lo + 2^31) >u ~F as a signed compare
     }
 #pragma unroll
     for (int m = 1; m * f.q <= HS_HMAX_2D; ++m) S[m * f.q] = add2(S[m * f.q], v);
 }
 
 template <int... K>
-__device__ __forceinline__ void farey16_pair_all(const float* plane, uint32_t stride, int z, int z_min, uint32_t n,
-                                                 uint32_t nmax, float2 (&S)[HS_HMAX_2D + 1],
-                                                 std::integer_sequence<int, K...>) {
-    (farey16_pair_step<K>(plane, stride, z, z_min, n, nmax, S), ...);
+__device__ __forceinline__ void farey16_pair_all(const float* plane, int z, uint32_t stride, uint32_t base, uint32_t n,
+                                                 float2 (&S)[HS_HMAX_2D + 1], std::integer_sequence<int, K...>) {
+    (farey16_pair_step<K>(plane, z, stride, base, n, S), ...);
 }
 
 __global__ void __launch_bounds__(k2dGroups * 32, 2) k_hs2d_pairs(const __grid_constant__ Tables tb, const Work2d w,
@@ -179,10 +184,12 @@ __global__ void __launch_bounds__(k2dGroups * 32, 2) k_hs2d_pairs(const __grid_c
     __shared__ int s_row[k2dGroups][k2dPairBins];
     __shared__ int s_h[k2dGroups][k2dPairBins];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const uint32_t nb = (uint32_t)w.n_bins;
+    const uint32_t nb = (uint32_t)w.n_bins;  // even and >= 2 on this path
     const uint32_t n = blockIdx.x * k2dPairBins + 2 * lane;  // this lane's bins n and n+1
     const bool act0 = n < nb, act1 = n + 1 < nb;
-    const uint32_t nq = act0 ? n : nb - 1;  // keep every read inside the row
+    const uint32_t nq = act0 ? n : nb - 2;  // idle lanes evaluate the last pair of the row
+    const uint32_t stride = (uint32_t)w.row_stride;
+    const uint32_t base = (uint32_t)(-(32768 + w.z_min)) * stride;
     float rb[2] = {-INFINITY, -INFINITY};
     int rr[2] = {0x7fffffff, 0x7fffffff}, rh[2] = {0, 0};
     for (int r = g; r < w.nz; r += k2dGroups) {
@@ -190,8 +197,7 @@ __global__ void __launch_bounds__(k2dGroups * 32, 2) k_hs2d_pairs(const __grid_c
         float2 S[HS_HMAX_2D + 1];
 #pragma unroll
         for (int H = 0; H <= HS_HMAX_2D; ++H) S[H] = make_float2(0.f, 0.f);
-        farey16_pair_all(w.plane, (uint32_t)w.row_stride, z, w.z_min, nq, nb - 1, S,
-                         std::make_integer_sequence<int, kNumFrac16>{});
+        farey16_pair_all(w.plane, z, stride, base, nq, S, std::make_integer_sequence<int, kNumFrac16>{});
         float b0 = -INFINITY, b1 = -INFINITY;
         int h0 = 0, h1 = 0;
 #pragma unroll
