@@ -58,6 +58,9 @@ def parse():
                     help="Eq. 1 with its input spans staged in shared memory by bulk copies (HS_FLAG_STAGED_SPANS)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the FP16/BF16, adjoint and 2-D measurements reported beside the main line")
+    ap.add_argument("--section", default="", choices=("", "precision", "upstream", "adjoint", "fdas_2d"),
+                    help="run only this secondary workload and print its JSON (for profiling one kernel)")
+    ap.add_argument("--fdas-bins", type=int, default=1 << 21, help="bins per row of the 2-D planes")
     return ap.parse_args()
 
 
@@ -249,11 +252,21 @@ def _time_ms(torch, stream, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
-def secondary(torch, hs, stream, tiles=None, reps=2):
+def secondary(torch, hs, stream, tiles=None, reps=2, only="", fdas_bins=1 << 21):
     """The batched (FP16/BF16 storage), adjoint and 2-D forms on their own workloads, each next to
-    the plain FP32 path on the same GPU.  Inputs are device-generated noise of the workload shapes."""
+    the plain FP32 path on the same GPU.  Inputs are device-generated noise of the workload shapes.
+    ``only`` names one section to run alone."""
     out = {}
-    # precision: 4096 spectra x 2^20 bins stored FP16 and BF16 after standardisation
+    for name, fn in (("precision", _sec_precision), ("upstream", _sec_upstream), ("adjoint", _sec_adjoint),
+                     ("fdas_2d", _sec_fdas_2d)):
+        if not only or only == name:
+            out[name] = fn(torch, hs, stream, tiles, reps, fdas_bins)
+            torch.cuda.empty_cache()
+    return out
+
+
+def _sec_precision(torch, hs, stream, tiles, reps, fdas_bins):
+    # 4096 spectra x 2^20 bins stored FP16 and BF16 after standardisation
     n_s, n_b = 4096, 1 << 20
     total = n_s * n_b
     od = (torch.arange(n_s + 1, device="cuda", dtype=torch.int64) * n_b)
@@ -293,11 +306,10 @@ def secondary(torch, hs, stream, tiles=None, reps=2):
         torch.cuda.empty_cache()
     for name in ("f16", "bf16"):
         res[name]["speedup_vs_f32"] = res["f32"]["ms_per_step"] / res[name]["ms_per_step"]
-    out["precision"] = {"workload": "4096 spectra x 2^20 bins, standardised Exp(1) noise, all four variants",
-                        **res}
-    del p, mu, sd, od
-    torch.cuda.empty_cache()
+    return {"workload": "4096 spectra x 2^20 bins, standardised Exp(1) noise, all four variants", **res}
 
+
+def _sec_upstream(torch, hs, stream, tiles, reps, fdas_bins):
     # the step before the sums: power of complex spectra, block-median dereddening (128 bins),
     # standardisation, FP16 store; 1024 spectra x 2^20 complex bins (8 GiB in, 2 GiB out)
     n_s, n_b = 1024, 1 << 20
@@ -313,13 +325,13 @@ def secondary(torch, hs, stream, tiles=None, reps=2):
     compulsory = n_s * n_b * (8 + 2)  # complex in, FP16 out
     moved = n_s * n_b * (8 + 8 + 2)  # the median pass and the normalising pass each read the input
     peaks, _ = load_peaks()
-    out["upstream"] = {"workload": "1024 spectra x 2^20 complex bins -> FP16, blocks of 128 bins",
-                       "ms": ms, "gbs_compulsory": compulsory / (ms / 1e3) / 1e9,
-                       "gbs_moved": moved / (ms / 1e3) / 1e9,
-                       "frac_compulsory_of_hbm": compulsory / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
-    del spec, od, hu, med, out16
-    torch.cuda.empty_cache()
+    return {"workload": "1024 spectra x 2^20 complex bins -> FP16, blocks of 128 bins",
+            "ms": ms, "gbs_compulsory": compulsory / (ms / 1e3) / 1e9,
+            "gbs_moved": moved / (ms / 1e3) / 1e9,
+            "frac_compulsory_of_hbm": compulsory / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
 
+
+def _sec_adjoint(torch, hs, stream, tiles, reps, fdas_bins):
     # differentiation: 256 spectra x 2^20, Eq. 1 and Max, loss = sum softplus(snr - 5)
     n_s, n_b = 256, 1 << 20
     total = n_s * n_b
@@ -347,12 +359,12 @@ def secondary(torch, hs, stream, tiles=None, reps=2):
         adj[v] = {"forward_ms": fwd, "backward_ms": b, "backward_over_forward": b / fwd,
                   "value_fwd_bwd": total * HMAX / ((fwd + b) / 1e3)}
         del h, o, g, gx
-    out["adjoint"] = {"workload": "256 spectra x 2^20 bins FP32, loss = sum softplus(snr - 5)", **adj}
-    del x, od
-    torch.cuda.empty_cache()
+    return {"workload": "256 spectra x 2^20 bins FP32, loss = sum softplus(snr - 5)", **adj}
 
+
+def _sec_fdas_2d(torch, hs, stream, tiles, reps, fdas_bins):
     # 2-D: 16 FDAS planes of 201 z rows x 2^21 bins, H = 1..16
-    nz, z_min, n_b, planes = 201, -100, 1 << 21, 16
+    nz, z_min, n_b, planes = 201, -100, fdas_bins, 16
     plane = _noise(torch, (nz, n_b), 3000)
     h = hs.HarmonicSum(variants=hs.STD, hmax=16, nz=nz, z_min=z_min, max_bins=n_b, threshold=THR,
                        cand_capacity=1 << 24)
@@ -363,15 +375,11 @@ def secondary(torch, hs, stream, tiles=None, reps=2):
     of = hf.sum_2d(plane, stream=stream, variant="fbin")
     per_plane_fbin = _time_ms(torch, stream, lambda: (of["cand_count"].zero_(),
                                                       hf.sum_2d(plane, out=of, stream=stream, variant="fbin")), reps)
-    out["fdas_2d"] = {"workload": "16 planes x 201 rows x 2^21 bins FP32, H = 1..16 (timed per plane, same plane)",
-                      "ms_per_plane": per_plane, "ms_per_16_planes": per_plane * planes,
-                      "cells_per_s": nz * n_b / (per_plane / 1e3),
-                      "harmonic_summed_cells_per_s": nz * n_b * 16 / (per_plane / 1e3),
-                      "fbin_ms_per_plane": per_plane_fbin}
-    del hf, of
-    del plane, o, h
-    torch.cuda.empty_cache()
-    return out
+    return {"workload": "16 planes x 201 rows x %d bins FP32, H = 1..16 (timed per plane, same plane)" % n_b,
+            "ms_per_plane": per_plane, "ms_per_16_planes": per_plane * planes,
+            "cells_per_s": nz * n_b / (per_plane / 1e3),
+            "harmonic_summed_cells_per_s": nz * n_b * 16 / (per_plane / 1e3),
+            "fbin_ms_per_plane": per_plane_fbin}
 
 
 def main():
@@ -382,6 +390,13 @@ def main():
 
     import paper_1812_02647_gb300 as hs
 
+    if args.section:
+        stream = torch.cuda.Stream()
+        with torch.cuda.stream(stream):
+            print(json.dumps({"section": args.section,
+                              **secondary(torch, hs, stream, reps=max(args.steps, 1), only=args.section,
+                                          fdas_bins=args.fdas_bins)}))
+        return 0
     rank, world, local = dist_setup()
     variants = tuple(args.variants.split(","))
     seed, offsets, pulsars = rank_workload(args.spectra, rank)
@@ -623,7 +638,7 @@ def main():
         del graphs, outs, xd
         torch.cuda.empty_cache()
         with torch.cuda.stream(stream):
-            line["secondary"] = secondary(torch, hs, stream, tiles=tuned)
+            line["secondary"] = secondary(torch, hs, stream, tiles=tuned, fdas_bins=args.fdas_bins)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         n_s = min(args.cpu_sample_spectra, args.spectra)

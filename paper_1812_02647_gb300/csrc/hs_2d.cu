@@ -156,15 +156,18 @@ __device__ __forceinline__ void farey16_pair_step(const float* plane, int z, uin
                                                   float2 (&S)[HS_HMAX_2D + 1]) {
     constexpr Frac16 f = farey16_at(K);
     const uint32_t roff = row_offset16<f.p, f.q>(z, stride, base);
+    // the second read goes through the pointer (p + 1), so it shares the first read's address
     float2 v;
     if (f.q == 1) {
-        v.x = __ldg(plane + (roff + n));
-        v.y = __ldg(plane + (roff + n + 1));
+        const float* p = plane + (roff + n);
+        v.x = __ldg(p);
+        v.y = __ldg(p + 1);
     } else {
         constexpr uint32_t F = (uint32_t)((((uint64_t)f.p << 32) + f.q - 1) / f.q);
         const uint32_t lo = n * F;
         const uint32_t k = __umulhi(n, F) + (lo >> 31);
-        const float a = __ldg(plane + (roff + k)), b = __ldg(plane + (roff + k + 1));
+        const float* p = plane + (roff + k);
+        const float a = __ldg(p), b = __ldg(p + 1);
         v.x = a;
         v.y = ((int32_t)lo > (int32_t)(~F ^ 0x80000000u)) ? b : a;  // (lo + 2^31) >u ~F as a signed compare
     }
