@@ -206,8 +206,8 @@ struct Bin<HS_GREEDY, T> {
             if (fixed1 && i == 1) {
                 S = __fadd_rn(S, ldx(x, n));
             } else {
-                const uint32_t b = (uint32_t)i * n + j;
-                const float l = ldx(x, b), r = ldx(x, b + 1);
+                const T* q = x + ((uint32_t)i * n + j);  // r through q + 1: no address of its own
+                const float l = widen<T>(__ldg(q)), r = widen<T>(__ldg(q + 1));
                 const bool right = r > l;
                 p |= (right ? 1u : 0u) << (i - 1);
                 j += right ? 1u : 0u;
