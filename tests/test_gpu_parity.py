@@ -345,6 +345,28 @@ def test_2d_generic_and_edge_paths(hs_lib, torch, nb, hmax):
     np.testing.assert_array_equal(o["best_z_n"].cpu().numpy().astype(np.int32), r["best_z_n"])
 
 
+@pytest.mark.parametrize("variant", ["std", "fbin"])
+@pytest.mark.parametrize("z_min,nz,nb", [(-32766, 32767, 64), (0, 32767, 64), (-300, 301, 130), (-32766, 32767, 63)])
+def test_2d_extreme_drift_ranges(hs_lib, torch, variant, z_min, nz, nb):
+    """Rows at the ends of the drift range the ABI accepts (|z| up to 32766), ranges on one side of
+    z = 0 only, and rows padded to a longer stride: every output equal to the oracle's."""
+    plane, _ = hs_synth.fdas_plane(7, nz=nz, z_min=z_min, n_bins=nb)
+    stride = (nb + 3) // 4 * 4
+    padded = torch.zeros((nz, stride), device="cuda")
+    padded[:, :nb] = torch.from_numpy(plane).cuda()
+    hs = hs_lib.HarmonicSum(variants=hs_lib.VARIANTS[variant], hmax=16, nz=nz, z_min=z_min, max_bins=nb,
+                            threshold=THR, cand_capacity=1 << 20)
+    o = hs.sum_2d(padded[:, :nb], variant=variant)
+    assert hs.sync_status() == hs_lib.OK
+    r = oracle.hs_2d(plane, z_min, hmax=16, variant=variant, nthreads=8)
+    np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+    np.testing.assert_array_equal(o["best_snr_n"].cpu().numpy(), r["best_snr_n"])
+    np.testing.assert_array_equal(o["best_h_n"].cpu().numpy(), r["best_h_n"])
+    np.testing.assert_array_equal(o["best_z_n"].cpu().numpy().astype(np.int32), r["best_z_n"])
+    assert int(o["cand_count"].item()) == int((r["best_snr"] > THR).sum())
+
+
 def test_2d_full_size_sampled(hs_lib, torch):
     nz, z_min, nb = 201, -100, 1 << 21
     plane, _ = hs_synth.fdas_plane(3, nz=nz, z_min=z_min, n_bins=nb)
