@@ -160,7 +160,8 @@ struct Bin<HS_MAX, T> {
     }
 };
 
-// Eq. 3: harmonic i adds x(i*n).  Harmonics run up to the bin's own valid count, four loads at a time.
+// Eq. 3: harmonic i adds x(i*n).  Harmonics run up to the bin's own valid count, four loads at a time;
+// the loop is unrolled, so each harmonic's calibration constants are compile-time operands.
 template <typename T>
 struct Bin<HS_FBIN, T> {
     template <bool P2>
@@ -169,7 +170,9 @@ struct Bin<HS_FBIN, T> {
                                                 uint32_t& path, uint32_t flags) {
         const int hv = (n == 0) ? hmax : (int)min((uint32_t)hmax, (N - 1) / n);
         float S = 0.f;
-        for (int i0 = 1; i0 <= hv; i0 += 4) {
+#pragma unroll
+        for (int i0 = 1; i0 <= kHmax; i0 += 4) {
+            if (i0 > hv) break;
             float v[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) v[k] = (i0 + k <= hv) ? ldx(x, (uint32_t)(i0 + k) * n) : 0.f;
@@ -202,7 +205,9 @@ struct Bin<HS_GREEDY, T> {
         const int hv = N >= 1 ? (int)min((uint32_t)hmax, (fixed1 ? N : N - 1) / (n + 1)) : 0;
         float S = 0.f;
         uint32_t j = 0, p = 0;
-        for (int i = 1; i <= hv; ++i) {
+#pragma unroll
+        for (int i = 1; i <= kHmax; ++i) {
+            if (i > hv) break;
             if (fixed1 && i == 1) {
                 S = __fadd_rn(S, ldx(x, n));
             } else {
@@ -273,11 +278,12 @@ struct MinBlocks {
     static constexpr int value = V == HS_STD ? 2 : 6;
 };
 
-// Eq. 2-4 index the calibration tables by a runtime H, which is cheaper from shared memory than
-// from the kernel-parameter bank; Eq. 1 unrolls H and reads the parameter bank directly.
+// Eq. 2 indexes the calibration tables by a runtime H, which is cheaper from shared memory than
+// from the kernel-parameter bank; Eq. 1, 3 and 4 unroll H (the loop leaves at the bin's valid count)
+// and read the parameter bank directly.
 template <int V>
 __device__ __forceinline__ const Tables& stage_tables(const Tables& tb, Tables& smem) {
-    if (V != HS_STD) {
+    if (V == HS_MAX) {
         for (int k = threadIdx.x; k < 3 * (kHmax + 1); k += blockDim.x)
             reinterpret_cast<float*>(&smem)[k] = reinterpret_cast<const float*>(&tb)[k];
         __syncthreads();
