@@ -60,7 +60,7 @@ __device__ __forceinline__ void farey_pair_all(const T* x, uint32_t n, float2 (&
 template <typename T>
 struct Bin<HS_STD, T> {
     template <bool P2>
-    static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
+    static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, int hv, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path, uint32_t flags) {
         float S[kHmax + 1];
@@ -141,10 +141,9 @@ __device__ __forceinline__ float window_max(const T* x, uint32_t N, uint32_t w0,
 template <typename T>
 struct Bin<HS_MAX, T> {
     template <bool P2>
-    static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
+    static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, int hv, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path, uint32_t flags) {
-        const int hv = N >= 1 ? (int)min((uint32_t)hmax, (N - 1) / (n + 1)) : 0;
         const uint32_t j0 = (flags & HS_FLAG_MAX_WINDOW0) ? 0u : 1u;
         float S = 0.f;
         for (int i = 1; i <= hv; ++i) {
@@ -165,10 +164,9 @@ struct Bin<HS_MAX, T> {
 template <typename T>
 struct Bin<HS_FBIN, T> {
     template <bool P2>
-    static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
+    static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, int hv, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path, uint32_t flags) {
-        const int hv = (n == 0) ? hmax : (int)min((uint32_t)hmax, (N - 1) / n);
         float S = 0.f;
 #pragma unroll
         for (int i0 = 1; i0 <= kHmax; i0 += 4) {
@@ -198,11 +196,10 @@ struct Bin<HS_FBIN, T> {
 template <typename T>
 struct Bin<HS_GREEDY, T> {
     template <bool P2>
-    static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, const Tables& tb,
+    static __device__ __forceinline__ void eval(const T* x, uint32_t N, uint32_t n, int hmax, int hv, const Tables& tb,
                                                 float* all_h, uint32_t all_stride, float& best, int& bh,
                                                 uint32_t& path, uint32_t flags) {
         const bool fixed1 = (flags & HS_FLAG_GREEDY_FIXED1) != 0;
-        const int hv = N >= 1 ? (int)min((uint32_t)hmax, (fixed1 ? N : N - 1) / (n + 1)) : 0;
         float S = 0.f;
         uint32_t j = 0, p = 0;
 #pragma unroll
@@ -226,6 +223,36 @@ struct Bin<HS_GREEDY, T> {
         if (all_h)
             for (int i = hv + 1; i <= hmax; ++i) all_h[(size_t)(i - 1) * all_stride + n] = -INFINITY;
         path = p;
+    }
+};
+
+// ------------------------------------------------------------------------------------------
+// Valid harmonic count of output bin n (N >= 1): the largest H <= hmax whose reads stay inside the
+// spectrum.  Eq. 2: H (n+1) <= N-1; Eq. 3: H n <= N-1 (every H at n = 0); Eq. 4: H (n+1) <= N-1, or
+// <= N under the fixed first term; Eq. 1: always hmax.  It never grows with n, so for Eq. 3 and 4 a
+// thread divides once for its first bin of a tile and then steps it down as its bins advance (Eq. 2,
+// bound by load latency, ran slower that way and divides for every bin).
+// ------------------------------------------------------------------------------------------
+template <int V>
+struct ValidH {
+    static __device__ __forceinline__ uint32_t limit(uint32_t N, uint32_t flags) {
+        return (V == HS_GREEDY && (flags & HS_FLAG_GREEDY_FIXED1)) ? N : N - 1;
+    }
+    static __device__ __forceinline__ uint32_t span(uint32_t n) {
+        return V == HS_FBIN ? n : n + 1;
+    }
+    static __device__ __forceinline__ int first(uint32_t N, uint32_t n, int hmax, uint32_t flags) {
+        if (V == HS_STD) return hmax;
+        const uint32_t d = span(n);
+        return d == 0 ? hmax : (int)min((uint32_t)hmax, limit(N, flags) / d);
+    }
+    static __device__ __forceinline__ int step(int hv, uint32_t N, uint32_t n, uint32_t flags) {
+        if (V == HS_MAX) return (int)min((uint32_t)hv, limit(N, flags) / span(n));
+        if (V != HS_STD) {
+            const uint32_t a = limit(N, flags), d = span(n);  // hv * d <= 2^31: n < N <= 2^26
+            while (hv > 0 && (uint32_t)hv * d > a) --hv;
+        }
+        return hv;
     }
 };
 
@@ -255,6 +282,7 @@ __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, ui
             }
         }
     }
+    int hv = ValidH<V>::first(N, base + threadIdx.x, w.hmax, (uint32_t)w.flags);
     for (; base < t1; base += kBlock) {
         uint32_t n = base + threadIdx.x;
         bool active = n < t1;
@@ -262,7 +290,8 @@ __device__ __forceinline__ void run_tile(const T* x, uint32_t N, uint32_t t0, ui
         int bh = 0;
         uint32_t path = 0;
         if (active) {
-            Bin<V, T>::template eval<P2>(x, N, n, w.hmax, tb, o.all_h, N, best, bh, path, (uint32_t)w.flags);
+            hv = ValidH<V>::step(hv, N, n, (uint32_t)w.flags);
+            Bin<V, T>::template eval<P2>(x, N, n, w.hmax, hv, tb, o.all_h, N, best, bh, path, (uint32_t)w.flags);
             o.best_snr[out_off + n] = best;
             o.best_h[out_off + n] = (uint8_t)bh;
             if (V == HS_GREEDY && o.path) o.path[out_off + n] = path;
