@@ -146,13 +146,30 @@ struct Bin<HS_MAX, T> {
                                                 uint32_t& path, uint32_t flags) {
         const uint32_t j0 = (flags & HS_FLAG_MAX_WINDOW0) ? 0u : 1u;
         float S = 0.f;
-        for (int i = 1; i <= hv; ++i) {
-            const uint32_t base = (uint32_t)i * n;
-            S = __fadd_rn(S, window_max(x, N, base + j0, base + (uint32_t)i));
+        auto add = [&](int i, float m) {
+            S = __fadd_rn(S, m);
             const bool stage = !P2 || is_pow2(i);
             const float snr = stage ? calibrate(tb, S, i) : -INFINITY;
             if (stage) keep_best(snr, i, best, bh);
             if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
+        };
+        // Harmonics 1 and 2 span at most three elements, read with plain loads (coalesced across the
+        // warp) instead of masked 16-byte chunks; valid H means 2n + 2 <= N - 1 for the second.
+        if (hv >= 1) {
+            const T* p = x + n;  // [n + j0, n + 1]
+            float m = widen<T>(__ldg(p + 1));
+            if (j0 == 0) m = fmaxf(m, widen<T>(__ldg(p)));
+            add(1, m);
+        }
+        if (hv >= 2) {
+            const T* p = x + 2 * n;  // [2n + j0, 2n + 2]
+            float m = fmaxf(widen<T>(__ldg(p + 1)), widen<T>(__ldg(p + 2)));
+            if (j0 == 0) m = fmaxf(m, widen<T>(__ldg(p)));
+            add(2, m);
+        }
+        for (int i = 3; i <= hv; ++i) {
+            const uint32_t base = (uint32_t)i * n;
+            add(i, window_max(x, N, base + j0, base + (uint32_t)i));
         }
         if (all_h)
             for (int i = hv + 1; i <= hmax; ++i) all_h[(size_t)(i - 1) * all_stride + n] = -INFINITY;
