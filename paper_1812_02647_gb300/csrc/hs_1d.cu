@@ -153,8 +153,8 @@ struct Bin<HS_MAX, T> {
             if (stage) keep_best(snr, i, best, bh);
             if (all_h) all_h[(size_t)(i - 1) * all_stride + n] = snr;
         };
-        // Harmonics 1 and 2 span at most three elements, read with plain loads (coalesced across the
-        // warp) instead of masked 16-byte chunks; valid H means 2n + 2 <= N - 1 for the second.
+        // Harmonics 1 to 4 span at most five elements, read with plain loads (coalesced across the
+        // warp) instead of masked 16-byte chunks; valid H means H n + H <= N - 1.
         if (hv >= 1) {
             const T* p = x + n;  // [n + j0, n + 1]
             float m = widen<T>(__ldg(p + 1));
@@ -167,7 +167,20 @@ struct Bin<HS_MAX, T> {
             if (j0 == 0) m = fmaxf(m, widen<T>(__ldg(p)));
             add(2, m);
         }
-        for (int i = 3; i <= hv; ++i) {
+        if (hv >= 3) {
+            const T* p = x + 3 * n;  // [3n + j0, 3n + 3]
+            float m = fmaxf(fmaxf(widen<T>(__ldg(p + 1)), widen<T>(__ldg(p + 2))), widen<T>(__ldg(p + 3)));
+            if (j0 == 0) m = fmaxf(m, widen<T>(__ldg(p)));
+            add(3, m);
+        }
+        if (hv >= 4) {
+            const T* p = x + 4 * n;  // [4n + j0, 4n + 4]
+            float m = fmaxf(fmaxf(widen<T>(__ldg(p + 1)), widen<T>(__ldg(p + 2))),
+                            fmaxf(widen<T>(__ldg(p + 3)), widen<T>(__ldg(p + 4))));
+            if (j0 == 0) m = fmaxf(m, widen<T>(__ldg(p)));
+            add(4, m);
+        }
+        for (int i = 5; i <= hv; ++i) {
             const uint32_t base = (uint32_t)i * n;
             add(i, window_max(x, N, base + j0, base + (uint32_t)i));
         }
