@@ -179,6 +179,14 @@ def cpu_oracle_sample(offsets, x_host, n_sample, variants, cores, reps=1):
     return bins, statistics.median(times)
 
 
+def cpu_single_thread(offsets, x_host, variants, n_sample=2):
+    """The oracle's FP32 mode on one host thread over the first n_sample spectra: the single-core
+    figure reported beside the all-cores one."""
+    bins, t = cpu_oracle_sample(offsets, x_host, n_sample, variants, 1)
+    return {"value": bins * HMAX / t, "unit": UNIT, "cores": 1,
+            "sample": "first %d spectra (%d bins), %s, FP32 oracle, one thread" % (n_sample, bins, "+".join(variants))}
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle on a bounded sample, rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
@@ -205,7 +213,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": workload_config(args, offsets, variants),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "single_thread": cpu_single_thread(offsets, x, variants)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -644,7 +653,8 @@ def main():
         n_s = min(args.cpu_sample_spectra, args.spectra)
         bins, t = cpu_oracle_sample(offsets, x_host.numpy(), n_s, variants, cores)
         line["cpu_baseline"] = {"value": bins * HMAX / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "first %d spectra (%d bins), all listed variants, FP32 oracle" % (n_s, bins)}
+                                "sample": "first %d spectra (%d bins), all listed variants, FP32 oracle" % (n_s, bins),
+                                "single_thread": cpu_single_thread(offsets, x_host.numpy(), variants)}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
