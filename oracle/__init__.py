@@ -59,6 +59,8 @@ def _load():
             getattr(lib, "hs_oracle_batched_" + sfx).argtypes = [I, P, P, I, I, P, P, P, P, P, I]
             getattr(lib, "hs_oracle_2d_" + sfx).argtypes = [P, I, I, I64, I64, I, P, P, P, P, P, P, P, P, I]
             getattr(lib, "hs_oracle_2d_fbin_" + sfx).argtypes = [P, I, I, I64, I64, I, P, P, P, P, P, P, P, P, I]
+            getattr(lib, "hs_oracle_2d_rowwise_" + sfx).argtypes = [I, P, I, I, I64, I64, I, P, P, P, P, P, P, P, P,
+                                                                    I]
         lib.hs_oracle_grad_f64.argtypes = [I, P, I64, I, P, P, P, P]
         lib.hs_oracle_standardize_cast.argtypes = [P, I64, ctypes.c_float, ctypes.c_float, I, P]
         lib.hs_oracle_noise_moments.argtypes = [I, I, P, P]
@@ -163,8 +165,9 @@ def hs_batched(variant, x, offsets, hmax: int = 32, mu=None, isig=None, fp64: bo
 
 def hs_2d(plane, z_min: int, hmax: int = 16, mu=None, isig=None, fp64: bool = False, all_h: bool = False,
           nthreads: int | None = None, variant: str = "std"):
-    """2-D Eq. 1 (variant "std") or its freq-bin form ("fbin": harmonic i at (i n, i z)) over a
-    (nz, n_bins) plane whose row r holds z = z_min + r."""
+    """2-D Eq. 1 (variant "std") or the row-wise 2-D forms of Eq. 2-4 ("fbin": harmonic i at
+    (i n, i z); "max", "max0", "greedy", "greedy1": harmonic i taken on the row i z as the 1-D
+    equation takes it) over a (nz, n_bins) plane whose row r holds z = z_min + r."""
     dt = np.float64 if fp64 else np.float32
     plane = np.ascontiguousarray(plane, dtype=dt)
     nz, nb = plane.shape
@@ -179,8 +182,14 @@ def hs_2d(plane, z_min: int, hmax: int = 16, mu=None, isig=None, fp64: bool = Fa
         fn = _load().hs_oracle_2d_f64 if fp64 else _load().hs_oracle_2d_f32
     elif variant == "fbin":
         fn = _load().hs_oracle_2d_fbin_f64 if fp64 else _load().hs_oracle_2d_fbin_f32
+    elif variant in ("max", "max0", "greedy", "greedy1"):
+        row = _load().hs_oracle_2d_rowwise_f64 if fp64 else _load().hs_oracle_2d_rowwise_f32
+        v = _variant(variant)
+
+        def fn(*a):
+            return row(v, *a)
     else:
-        raise ValueError("2-D sums are defined for std and fbin")
+        raise ValueError("unknown 2-D variant %r" % variant)
     fn(_ptr(plane), nz, z_min, nb, nb, hmax, _ptr(mu), _ptr(isig), _ptr(best), _ptr(bh), _ptr(bn), _ptr(bhn),
        _ptr(bzn), _ptr(ah), _threads(nthreads))
     out = {"best_snr": best, "best_h": bh, "best_snr_n": bn, "best_h_n": bhn, "best_z_n": bzn}

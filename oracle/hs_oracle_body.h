@@ -251,6 +251,97 @@ void FN(hs_oracle_2d_fbin_)(const REAL* plane, int nz, int z_min, int64_t n_bins
     }
 }
 
+/*
+ * 2-D forms of Eq. 2 and Eq. 4 (a reading: the paper writes these two sums in 1-D only).  As in the
+ * 2-D form of Eq. 3, harmonic i of the cell (n, z) lies on the row i*z, and within that row it is
+ * taken exactly as the 1-D equation takes it: Eq. 2 the largest of x(i*n+j0 .. i*n+i, i*z) (j0 = 1,
+ * or 0 under MAX0), first maximum; Eq. 4 the choice between x(i*n+j, i*z) and x(i*n+j+1, i*z), the
+ * right one only when strictly larger, j carried from harmonic to harmonic (GREEDY1: the first term
+ * is x(n, z) and the pairs start at harmonic 2).  Terms are added in the order i = 1..H.  H is valid
+ * while the 1-D rule holds for n (H*(n+1) <= N-1, or <= N under GREEDY1) and H*z stays within the
+ * plane's rows.  Per bin n the best over rows keeps the lowest row on ties.
+ */
+void FN(hs_oracle_2d_rowwise_)(int variant, const REAL* plane, int nz, int z_min, int64_t n_bins,
+                               int64_t row_stride, int hmax, const REAL* mu_in, const REAL* isig_in, REAL* best_snr,
+                               uint8_t* best_h, REAL* best_snr_n, uint8_t* best_h_n, int32_t* best_z_n, REAL* all_h,
+                               int nthreads) {
+    REAL cs[HS_O_HMAX + 1], mu[HS_O_HMAX + 1], isig[HS_O_HMAX + 1];
+    for (int H = 0; H <= hmax; ++H) {
+        cs[H] = (H == 0) ? (REAL)0 : (REAL)(1.0 / sqrt((double)H));
+        mu[H] = mu_in ? mu_in[H] : (REAL)0;
+        isig[H] = isig_in ? isig_in[H] : (REAL)1;
+    }
+    const int64_t z_max = (int64_t)z_min + nz - 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) if (nthreads > 1)
+    for (int r = 0; r < nz; ++r) {
+        const int64_t z = (int64_t)z_min + r;
+        for (int64_t n = 0; n < n_bins; ++n) {
+            const int hv = hs_oracle_hvalid(variant, n, n_bins, hmax);
+            REAL best = -INFINITY, S = 0;
+            int bh = 0;
+            int64_t j = 0;
+            for (int H = 1; H <= hmax; ++H) {
+                REAL snr = -INFINITY;
+                const int valid = H <= hv && H * z >= z_min && H * z <= z_max;
+                if (valid) {
+                    const REAL* row = plane + (H * z - z_min) * row_stride;
+                    REAL t;
+                    if (variant == HS_O_MAX || variant == HS_O_MAX0) {
+                        const int64_t base = (int64_t)H * n;
+                        const int jfirst = (variant == HS_O_MAX0) ? 0 : 1;
+                        t = row[base + jfirst];
+                        for (int jw = jfirst + 1; jw <= H; ++jw) {
+                            REAL v = row[base + jw];
+                            t = (v > t) ? v : t;
+                        }
+                    } else if (H == 1 && variant == HS_O_GREEDY1) { /* first term fixed at x(n, z) */
+                        t = row[n];
+                    } else { /* HS_O_GREEDY (and GREEDY1 from H = 2 on) */
+                        const int64_t base = (int64_t)H * n + j;
+                        REAL lft = row[base], rgt = row[base + 1];
+                        if (rgt > lft) {
+                            t = rgt;
+                            j += 1;
+                        } else {
+                            t = lft;
+                        }
+                    }
+                    S = S + t;
+                    REAL h = S * cs[H];
+                    snr = (h - mu[H]) * isig[H];
+                    if (snr > best) {
+                        best = snr;
+                        bh = H;
+                    }
+                }
+                if (all_h) all_h[((int64_t)(H - 1) * nz + r) * n_bins + n] = snr;
+                if (!valid) { /* later H are invalid too: the rows H*z move further out */
+                    for (int H2 = H + 1; H2 <= hmax; ++H2)
+                        if (all_h) all_h[((int64_t)(H2 - 1) * nz + r) * n_bins + n] = -INFINITY;
+                    break;
+                }
+            }
+            best_snr[(int64_t)r * n_bins + n] = best;
+            best_h[(int64_t)r * n_bins + n] = (uint8_t)bh;
+        }
+    }
+#pragma omp parallel for schedule(static) num_threads(nthreads > 0 ? nthreads : 1) if (nthreads > 1)
+    for (int64_t n = 0; n < n_bins; ++n) {
+        REAL best = -INFINITY;
+        int br = 0;
+        for (int r = 0; r < nz; ++r) {
+            REAL v = best_snr[(int64_t)r * n_bins + n];
+            if (v > best) {
+                best = v;
+                br = r;
+            }
+        }
+        best_snr_n[n] = best;
+        best_h_n[n] = best_h[(int64_t)br * n_bins + n];
+        best_z_n[n] = z_min + br;
+    }
+}
+
 void FN(hs_oracle_2d_cells_)(const REAL* plane, int nz, int z_min, int64_t n_bins, int64_t row_stride, int hmax,
                              const REAL* mu_in, const REAL* isig_in, const int32_t* rows, const int64_t* bins,
                              int64_t count, REAL* best_snr, uint8_t* best_h) {

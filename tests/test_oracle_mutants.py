@@ -79,6 +79,17 @@ MUTANTS = [
      ["test_standardize_cast_f16_matches_ieee_library"]),
     ("max noise mean drops the -1 of the standardised terms", "hs_oracle.c", "m_acc += harm - 1.0;",
      "m_acc += harm;", ["test_noise_calibration_tables"]),
+    ("2-D row-wise forms read row z for every harmonic", "hs_oracle_body.h",
+     "const REAL* row = plane + (H * z - z_min) * row_stride;", "const REAL* row = plane + (z - z_min) * row_stride;",
+     ["test_2d_rowwise_reads_only_rows_i_z", "test_2d_rowwise_max_delta_spike"]),
+    ("2-D row-wise greedy takes the right bin on ties", "hs_oracle_body.h", "if (rgt > lft) {", "if (rgt >= lft) {",
+     ["test_2d_rowwise_zero_row_is_1d_and_ranges"]),
+    ("2-D row-wise max window ends one bin early", "hs_oracle_body.h",
+     "for (int jw = jfirst + 1; jw <= H; ++jw) {", "for (int jw = jfirst + 1; jw < H; ++jw) {",
+     ["test_2d_rowwise_max_delta_spike", "test_2d_rowwise_zero_row_is_1d_and_ranges"]),
+    ("2-D row-wise drift range one row short", "hs_oracle_body.h",
+     "const int valid = H <= hv && H * z >= z_min && H * z <= z_max;",
+     "const int valid = H <= hv && H * z > z_min && H * z <= z_max;", ["test_2d_rowwise_zero_row_is_1d_and_ranges"]),
 ]
 
 
@@ -107,7 +118,10 @@ def _run_pin(name):
               "test_calibration_closed_form": [(v,) for v in pins.VARIANTS],
               "test_pow2_stages_restrict_the_full_search": [(v,) for v in pins.VARIANTS],
               "test_power_normalize_medians_are_lower_order_statistics": [(1000, 128), (77, 128), (300, 256)],
-              "test_adjoint_is_transpose_of_linear_map": [("std",), ("fbin",)]}
+              "test_adjoint_is_transpose_of_linear_map": [("std",), ("fbin",)],
+              "test_2d_rowwise_zero_row_is_1d_and_ranges": [(v,) for v in pins.ROWWISE],
+              "test_2d_rowwise_reads_only_rows_i_z": [(v,) for v in pins.ROWWISE],
+              "test_2d_rowwise_constant_plane": [(v,) for v in pins.ROWWISE]}
     for args in params.get(name, [()]):
         fn(*args)
 

@@ -444,9 +444,10 @@ def test_adjoint_max_ties_route_to_first_maximum():
     np.testing.assert_allclose(grad, expect, rtol=1e-12, atol=1e-12)
 
 
-def _routing(variant, x, hmax):
-    """Everything that decides which bins a bin's best sum reads."""
-    r = oracle.hs_1d(variant, x, hmax=hmax, fp64=True, all_h=True)
+def _routing(variant, x, hmax, mu=None, isig=None):
+    """Everything that decides which bins a bin's best sum reads: the best H under the given
+    calibration (the one the gradient is routed through), the Eq. 4 path, the Eq. 2 argmaxes."""
+    r = oracle.hs_1d(variant, x, hmax=hmax, mu=mu, isig=isig, fp64=True, all_h=True)
     key = [r["best_h"].astype(np.int64)]
     if variant in GREEDY:
         key.append(r["path"].astype(np.int64))
@@ -474,11 +475,11 @@ def test_adjoint_finite_differences(variant):
     rng = np.random.default_rng(77)
     for s in range(n_spec):
         x = rand_spectrum(N, 700 + s).astype(np.float64)
-        r0, k0 = _routing(variant, x, hmax)
+        r0, k0 = _routing(variant, x, hmax, mu64, isig64)
         for d in range(2):
             v = rng.standard_normal(N)
-            rp, kp = _routing(variant, x + eps * v, hmax)
-            rm, km = _routing(variant, x - eps * v, hmax)
+            rp, kp = _routing(variant, x + eps * v, hmax, mu64, isig64)
+            rm, km = _routing(variant, x - eps * v, hmax, mu64, isig64)
             keep = (k0 == kp).all(0) & (k0 == km).all(0) & (r0["best_h"] > 0)
             # snr with the same calibration as the analytic side
             def snr(rr):
@@ -741,3 +742,86 @@ def test_2d_fbin_delta_spike_and_constant():
     for H in range(1, 17):
         v = c[H - 1][np.isfinite(c[H - 1])]
         np.testing.assert_allclose(v, 1.5 * math.sqrt(H), rtol=1e-14)
+
+
+# ---------------------------------------------------------------------------------------------
+# 2-D forms of Eq. 2 and Eq. 4 (a reading: harmonic i of the cell (n, z) taken on the row i z as the
+# 1-D equation takes it)
+# ---------------------------------------------------------------------------------------------
+
+ROWWISE = ["max", "max0", "greedy", "greedy1"]
+
+
+@pytest.mark.parametrize("variant", ROWWISE)
+def test_2d_rowwise_zero_row_is_1d_and_ranges(variant):
+    """Every harmonic of a z = 0 cell lies on row 0, so that row's results are the 1-D sums of the
+    row (including the Eq. 4 choices); row z keeps H while H z stays in the plane."""
+    nz, z_min, nb = 9, -4, 300
+    ties = np.random.default_rng(81).integers(0, 3, (nz, nb)).astype(np.float64)  # many equal neighbours
+    for plane in (ties, np.stack([rand_spectrum(nb, 80 + r) for r in range(nz)])):
+        for fp64 in (False, True):
+            r2 = oracle.hs_2d(plane, z_min, hmax=16, fp64=fp64, all_h=True, variant=variant)
+            r1 = oracle.hs_1d(variant, plane[-z_min], hmax=16, fp64=fp64, all_h=True)
+            np.testing.assert_array_equal(r2["all_h"][:, -z_min, :], r1["all_h"])
+            np.testing.assert_array_equal(r2["best_h"][-z_min], r1["best_h"])
+    for r in range(nz):
+        z = z_min + r
+        hz = 16 if z == 0 else (4 // abs(z))
+        for n in (0, 1, 7, 150, 298, 299):
+            hv = min(hz, oracle.hvalid(variant, n, nb, 16))
+            col = r2["all_h"][:, r, n]
+            assert np.isfinite(col[:hv]).all() and np.isneginf(col[hv:]).all(), (z, n, hv)
+
+
+@pytest.mark.parametrize("variant", ROWWISE)
+def test_2d_rowwise_reads_only_rows_i_z(variant):
+    """Changing every row that is not i z for some i <= H leaves the cell's sums up to H unchanged,
+    and changing row i z changes them."""
+    nz, z_min, nb = 15, -7, 160
+    plane = np.stack([rand_spectrum(nb, 90 + r) for r in range(nz)])
+    base = oracle.hs_2d(plane, z_min, hmax=16, fp64=True, all_h=True, variant=variant)["all_h"]
+    for z in (-3, -2, 2, 3):
+        used = {i * z for i in range(1, 17) if z_min <= i * z <= z_min + nz - 1}
+        other = plane.copy()
+        for rr in range(nz):
+            if z_min + rr not in used:
+                other[rr] = rand_spectrum(nb, 500 + rr)
+        got = oracle.hs_2d(other, z_min, hmax=16, fp64=True, all_h=True, variant=variant)["all_h"]
+        np.testing.assert_array_equal(got[:, z - z_min, :], base[:, z - z_min, :])
+        bumped = plane.copy()
+        bumped[2 * z - z_min] += 3.0  # row of harmonic 2
+        got = oracle.hs_2d(bumped, z_min, hmax=16, fp64=True, all_h=True, variant=variant)["all_h"]
+        ok = np.isfinite(base[1, z - z_min, :])
+        assert (got[1, z - z_min, ok] != base[1, z - z_min, ok]).any()
+
+
+@pytest.mark.parametrize("variant", ROWWISE)
+def test_2d_rowwise_constant_plane(variant):
+    """x = c everywhere: every window maximum and every choice (a tie keeps the left bin) is c, so
+    h_H = c sqrt(H) for every valid H."""
+    nz, z_min, nb = 11, -5, 120
+    c = oracle.hs_2d(np.full((nz, nb), 1.5), z_min, hmax=16, fp64=True, all_h=True, variant=variant)["all_h"]
+    for H in range(1, 17):
+        v = c[H - 1][np.isfinite(c[H - 1])]
+        assert v.size > 0
+        np.testing.assert_allclose(v, 1.5 * math.sqrt(H), rtol=1e-14)
+
+
+def test_2d_rowwise_max_delta_spike():
+    """One spike A at (m0, z0) of an otherwise zero plane: harmonic i of the cell (n, z) takes A exactly
+    when i z = z0 and m0 is in its window i n + 1 .. i n + i (i n .. i n + i for the window from 0)."""
+    nz, z_min, nb, A = 13, -6, 150, 2.0
+    m0, z0 = 97, -6
+    plane = np.zeros((nz, nb))
+    plane[z0 - z_min, m0] = A
+    for variant, j0 in (("max", 1), ("max0", 0)):
+        r = oracle.hs_2d(plane, z_min, hmax=16, fp64=True, all_h=True, variant=variant)["all_h"]
+        for rr in range(nz):
+            z = z_min + rr
+            for n in range(nb):
+                for H in range(1, 17):
+                    v = r[H - 1, rr, n]
+                    if not np.isfinite(v):
+                        continue
+                    hits = sum(1 for i in range(1, H + 1) if i * z == z0 and i * n + j0 <= m0 <= i * n + i)
+                    assert v == pytest.approx(A * hits / math.sqrt(H), abs=1e-15), (variant, z, n, H)
