@@ -53,12 +53,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default (or --tiles) tile sizes")
     ap.add_argument("--tiles", default="", help="variant=bins,... tile sizes to use instead of tuning")
-    ap.add_argument("--cpu-sample-spectra", type=int, default=16)
+    ap.add_argument("--cpu-sample-spectra", type=int, default=8)
     ap.add_argument("--staged-spans", action="store_true",
                     help="Eq. 1 with its input spans staged in shared memory by bulk copies (HS_FLAG_STAGED_SPANS)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the FP16/BF16, adjoint and 2-D measurements reported beside the main line")
-    ap.add_argument("--section", default="", choices=("", "precision", "upstream", "adjoint", "fdas_2d"),
+    ap.add_argument("--section", default="", choices=("", "config1", "precision", "upstream", "adjoint", "fdas_2d"),
                     help="run only this secondary workload and print its JSON (for profiling one kernel)")
     ap.add_argument("--fdas-bins", type=int, default=1 << 21, help="bins per row of the 2-D planes")
     return ap.parse_args()
@@ -162,18 +162,21 @@ def rank_workload(n_spectra, rank):
 
 
 def cpu_oracle_sample(offsets, x_host, n_sample, variants, cores, reps=1):
-    """Time the oracle's FP32 mode on the first n_sample spectra of the batch (all host cores,
-    one spectrum per thread as in the paper's CPU versions)."""
+    """Time the oracle's FP32 mode on the first n_sample spectra of the batch.  Each spectrum's bins
+    are split across the given host cores (the oracle's single-spectrum path: chunks of 2048 bins
+    handed out dynamically), so every core works however uneven the spectra are."""
     import oracle
 
     offs = offsets[: n_sample + 1].copy()
     xs = np.asarray(x_host[: int(offs[-1])])
+    tables = {v: oracle.noise_calibration(v, HMAX) for v in variants}
     times = []
     for _ in range(reps):
         t0 = time.perf_counter()
         for v in variants:
-            mu, isig = oracle.noise_calibration(v, HMAX)
-            oracle.hs_batched(v, xs, offs, hmax=HMAX, mu=mu, isig=isig, nthreads=cores)
+            mu, isig = tables[v]
+            for s in range(n_sample):
+                oracle.hs_1d(v, xs[int(offs[s]):int(offs[s + 1])], hmax=HMAX, mu=mu, isig=isig, nthreads=cores)
         times.append(time.perf_counter() - t0)
     bins = int(offs[-1])
     return bins, statistics.median(times)
@@ -197,7 +200,7 @@ def run_reference(args):
     oracle.build()
     variants = tuple(args.variants.split(","))
     seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(args.spectra)
-    n_sample = 4
+    n_sample = min(args.cpu_sample_spectra, args.spectra)  # the same sample as the main line's cpu_baseline
     x = hs_synth.batch(seed, offsets[: n_sample + 1], pulsars[:n_sample])
     cores = os.cpu_count() or 1
     for _ in range(args.warmup):
@@ -208,7 +211,8 @@ def run_reference(args):
         times.append(t)
     step = statistics.mean(times)
     value = bins * HMAX / step
-    sample = "%d of %d spectra (%d bins), %s" % (n_sample, args.spectra, bins, "+".join(variants))
+    sample = ("first %d of %d spectra (%d bins), %s, FP32 oracle, each spectrum's bins split across %d cores"
+              % (n_sample, args.spectra, bins, "+".join(variants), cores))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -262,16 +266,91 @@ def _time_ms(torch, stream, fn, reps):
 
 
 def secondary(torch, hs, stream, tiles=None, reps=2, only="", fdas_bins=1 << 21):
-    """The batched (FP16/BF16 storage), adjoint and 2-D forms on their own workloads, each next to
-    the plain FP32 path on the same GPU.  Inputs are device-generated noise of the workload shapes.
-    ``only`` names one section to run alone."""
+    """The single 131072-bin spectrum, the batched FP16/BF16 storage, the adjoint and the 2-D form on
+    their own workloads, each next to the plain FP32 path on the same GPU.  Inputs are device-generated
+    noise of the workload shapes (the single spectrum is the synthetic pulsar spectrum).  ``only``
+    names one section to run alone."""
     out = {}
-    for name, fn in (("precision", _sec_precision), ("upstream", _sec_upstream), ("adjoint", _sec_adjoint),
-                     ("fdas_2d", _sec_fdas_2d)):
+    for name, fn in (("config1", _sec_config1), ("precision", _sec_precision), ("upstream", _sec_upstream),
+                     ("adjoint", _sec_adjoint), ("fdas_2d", _sec_fdas_2d)):
         if not only or only == name:
             out[name] = fn(torch, hs, stream, tiles, reps, fdas_bins)
             torch.cuda.empty_cache()
     return out
+
+
+def fp64_sums(v, x, mu, isig, hmax=HMAX):
+    """Eq. 1-4 over every bin of one spectrum in FP64 (numpy), for the accuracy report of the
+    reduced-precision storage: best snr, best H, the snr of the runner-up H, and the Eq. 4 path.
+    Same readings as the library: round-half-up Eq. 1 index, Eq. 2 window j = 1..i, Eq. 4 ties
+    keep the left bin, harmonics truncated at the spectrum end, snr = (S/sqrt(H) - mu_H) isig_H."""
+    x = np.asarray(x, dtype=np.float64)
+    N = x.size
+    n = np.arange(N, dtype=np.int64)
+    mu64, is64 = np.asarray(mu, np.float64), np.asarray(isig, np.float64)
+    best = np.full(N, -np.inf)
+    second = np.full(N, -np.inf)
+    bh = np.zeros(N, np.int64)
+    path = np.zeros(N, np.uint32)
+
+    def keep(H, snr, ok):
+        snr = np.where(ok, snr, -np.inf)
+        up = snr > best
+        second[:] = np.where(up, best, np.maximum(second, snr))
+        best[up] = snr[up]
+        bh[up] = H
+
+    if v == "std":
+        for H in range(1, hmax + 1):
+            S = np.zeros(N)
+            for i in range(1, H + 1):
+                S += x[(2 * n * i + H) // (2 * H)]
+            keep(H, (S / np.sqrt(H) - mu64[H]) * is64[H], np.ones(N, bool))
+        return best, bh, second, path
+    S = np.zeros(N)
+    j = np.zeros(N, np.int64)
+    for i in range(1, hmax + 1):
+        ok = (i * n <= N - 1) if v == "fbin" else (i * (n + 1) <= N - 1)
+        m = n[ok]
+        if v == "fbin":
+            t = x[i * m]
+        elif v == "max":
+            t = x[i * m + 1]
+            for k in range(2, i + 1):
+                t = np.maximum(t, x[i * m + k])
+        else:
+            left, right = x[i * m + j[ok]], x[i * m + j[ok] + 1]
+            r = right > left
+            t = np.where(r, right, left)
+            path[m[r]] |= np.uint32(1 << (i - 1))
+            j[m[r]] += 1
+        S[ok] += t
+        keep(i, (S / np.sqrt(i) - mu64[i]) * is64[i], ok)
+    return best, bh, second, path
+
+
+def precision_accuracy(x32, got, mu, isig, tie=1e-3):
+    """Error of one variant's GPU outputs (best snr, best H, path) against FP64 on the same FP32
+    spectrum, and agreement beyond the tie margin."""
+    v = got["variant"]
+    b64, h64, s64, p64 = fp64_sums(v, x32, mu, isig)
+    snr = got["best_snr"].astype(np.float64)
+    ok = np.isfinite(b64)
+    flips = 0
+    if v == "greedy":
+        same = got["path"] == p64
+        flips = int((~same & ok).sum())
+        ok &= same
+    err = np.abs(snr[ok] - b64[ok])
+    clear = ok & (np.abs(b64 - THR) > tie)
+    cand = int(((snr > THR) != (b64 > THR))[clear].sum())
+    with np.errstate(invalid="ignore"):  # bins with a single valid H have no runner-up (-inf - -inf)
+        hclear = ok & (b64 - s64 > tie)
+    hdis = int((got["best_h"].astype(np.int64) != h64)[hclear].sum())
+    return {"max_abs_err_vs_fp64": float(err.max()) if err.size else 0.0,
+            "max_rel_err_vs_fp64": float((err / np.maximum(np.abs(b64[ok]), 1.0)).max()) if err.size else 0.0,
+            "candidates_disagreeing_beyond_tie": cand, "candidates_fp64": int((b64 > THR).sum()),
+            "best_h_disagreeing_beyond_tie": hdis, "greedy_path_flips": flips, "bins": int(x32.size)}
 
 
 def _sec_precision(torch, hs, stream, tiles, reps, fdas_bins):
@@ -280,6 +359,7 @@ def _sec_precision(torch, hs, stream, tiles, reps, fdas_bins):
     total = n_s * n_b
     od = (torch.arange(n_s + 1, device="cuda", dtype=torch.int64) * n_b)
     p = _noise(torch, (total,), 5000).add_(1.0)  # raw exponential power
+    x32_first = p[:n_b].sub(1.0).cpu().numpy()  # spectrum 0 in FP32: the FP64 accuracy reference's input
     mu = torch.ones(n_s, device="cuda")
     sd = torch.ones(n_s, device="cuda")
     res = {}
@@ -298,6 +378,7 @@ def _sec_precision(torch, hs, stream, tiles, reps, fdas_bins):
             hs.hs_plan_set_tile_bins(h.plan, v, bins)
         o = h.new_outputs(total, "greedy", "cuda")
         per = {}
+        acc = {}
         for v in VARIANTS:
             mu_v, isig_v = hs.hs_noise_calibration(v, HMAX)
             h.set_calibration(v, mu_v, isig_v)
@@ -307,15 +388,27 @@ def _sec_precision(torch, hs, stream, tiles, reps, fdas_bins):
                 hs.hs_sum_batched(h.plan, v, x, od, h.out_struct(o), h.ws, 0, stream)
 
             per[v] = _time_ms(torch, stream, run, reps)
+            stream.synchronize()
+            got = {"variant": v, "best_snr": o["best_snr"][:n_b].cpu().numpy(),
+                   "best_h": o["best_h"][:n_b].cpu().numpy(),
+                   "path": o["path"][:n_b].cpu().numpy().view(np.uint32)}
+            acc[v] = precision_accuracy(x32_first, got, mu_v, isig_v)
         step = sum(per.values())
         res[name] = {"ms_per_step": step, "per_variant_ms": per, "value": total * HMAX / (step / 1e3),
                      "input_bytes": total * x.element_size(), "cast_ms": cast_ms,
-                     "cast_gbs": None if cast_ms is None else total * (4 + 2) / (cast_ms / 1e3) / 1e9}
+                     "cast_gbs": None if cast_ms is None else total * (4 + 2) / (cast_ms / 1e3) / 1e9,
+                     "accuracy_spectrum0": acc}
         del x, o, h
         torch.cuda.empty_cache()
     for name in ("f16", "bf16"):
         res[name]["speedup_vs_f32"] = res["f32"]["ms_per_step"] / res[name]["ms_per_step"]
-    return {"workload": "4096 spectra x 2^20 bins, standardised Exp(1) noise, all four variants", **res}
+        res[name]["per_variant_speedup_vs_f32"] = {v: res["f32"]["per_variant_ms"][v] / res[name]["per_variant_ms"][v]
+                                                   for v in VARIANTS}
+    return {"workload": "4096 spectra x 2^20 bins, standardised Exp(1) noise, all four variants",
+            "accuracy": "spectrum 0 (2^20 bins) of each storage type against an FP64 numpy evaluation of Eq. 1-4 on "
+                        "its FP32 values; agreement counted where FP64 is more than 1e-3 from the threshold (candidates)"
+                        " or from the runner-up H (best H); Eq. 4 bins whose path differs from FP64's are counted as "
+                        "flips and left out of the error", **res}
 
 
 def _sec_upstream(torch, hs, stream, tiles, reps, fdas_bins):
@@ -372,23 +465,104 @@ def _sec_adjoint(torch, hs, stream, tiles, reps, fdas_bins):
 
 
 def _sec_fdas_2d(torch, hs, stream, tiles, reps, fdas_bins):
-    # 2-D: 16 FDAS planes of 201 z rows x 2^21 bins, H = 1..16
-    nz, z_min, n_b, planes = 201, -100, fdas_bins, 16
-    plane = _noise(torch, (nz, n_b), 3000)
+    # 2-D: 16 distinct FDAS planes of 201 z rows x 2^21 bins (27 GB), H = 1..16, each plane with its
+    # own outputs; one pass over all 16 planes is timed
+    nz, z_min, n_b, n_planes = 201, -100, fdas_bins, 16
+    planes = [_noise(torch, (nz, n_b), 3000 + k) for k in range(n_planes)]
     h = hs.HarmonicSum(variants=hs.STD, hmax=16, nz=nz, z_min=z_min, max_bins=n_b, threshold=THR,
                        cand_capacity=1 << 24)
-    o = h.sum_2d(plane, stream=stream)
-    per_plane = _time_ms(torch, stream, lambda: (o["cand_count"].zero_(), h.sum_2d(plane, out=o, stream=stream)), reps)
+    outs = [h.sum_2d(planes[0], stream=stream)]
+    outs += [{k: torch.empty_like(v) for k, v in outs[0].items()} for _ in range(n_planes - 1)]
+
+    def all_planes():
+        for k in range(n_planes):
+            outs[k]["cand_count"].zero_()
+            h.sum_2d(planes[k], plane_id=k, out=outs[k], stream=stream)
+
+    t16 = _time_ms(torch, stream, all_planes, reps)
+    cands = [int(o["cand_count"].item()) for o in outs]
     hf = hs.HarmonicSum(variants=hs.FBIN, hmax=16, nz=nz, z_min=z_min, max_bins=n_b, threshold=THR,
                         cand_capacity=1 << 24)
-    of = hf.sum_2d(plane, stream=stream, variant="fbin")
-    per_plane_fbin = _time_ms(torch, stream, lambda: (of["cand_count"].zero_(),
-                                                      hf.sum_2d(plane, out=of, stream=stream, variant="fbin")), reps)
-    return {"workload": "16 planes x 201 rows x %d bins FP32, H = 1..16 (timed per plane, same plane)" % n_b,
-            "ms_per_plane": per_plane, "ms_per_16_planes": per_plane * planes,
-            "cells_per_s": nz * n_b / (per_plane / 1e3),
-            "harmonic_summed_cells_per_s": nz * n_b * 16 / (per_plane / 1e3),
-            "fbin_ms_per_plane": per_plane_fbin}
+
+    def all_planes_fbin():
+        for k in range(n_planes):
+            outs[k]["cand_count"].zero_()
+            hf.sum_2d(planes[k], plane_id=k, out=outs[k], stream=stream, variant="fbin")
+
+    t16f = _time_ms(torch, stream, all_planes_fbin, reps)
+    rowwise = {}
+    for v in ("max", "greedy"):  # row-wise 2-D forms of Eq. 2 and 4 (harmonic i on row i z)
+        hv = hs.HarmonicSum(variants=hs.VARIANTS[v], hmax=16, nz=nz, z_min=z_min, max_bins=n_b, threshold=THR,
+                            cand_capacity=1 << 24)
+        mu, isig = hs.hs_noise_calibration(v, 16)
+        hv.set_calibration(v, mu, isig)
+
+        def all_planes_v(v=v, hv=hv):
+            for k in range(n_planes):
+                outs[k]["cand_count"].zero_()
+                hv.sum_2d(planes[k], plane_id=k, out=outs[k], stream=stream, variant=v)
+
+        rowwise[v] = _time_ms(torch, stream, all_planes_v, reps)
+    del planes, outs
+    cells = n_planes * nz * n_b
+    return {"workload": "16 distinct planes x 201 rows x %d bins FP32 (device noise), H = 1..16, one pass over all "
+                        "planes timed" % n_b,
+            "ms_per_16_planes": t16, "ms_per_plane": t16 / n_planes, "cells_per_s": cells / (t16 / 1e3),
+            "harmonic_summed_cells_per_s": cells * 16 / (t16 / 1e3), "candidates_per_plane": cands,
+            "fbin_ms_per_16_planes": t16f, "fbin_ms_per_plane": t16f / n_planes,
+            "max_ms_per_16_planes": rowwise["max"], "greedy_ms_per_16_planes": rowwise["greedy"]}
+
+
+def _sec_config1(torch, hs, stream, tiles, reps, fdas_bins):
+    # one 131072-bin spectrum with the injected pulsar (f0 = 1000.37, 16 harmonics, 8/k), all four
+    # variants through hs_sum_1d: per-variant device time of plain launches and of one CUDA graph
+    # holding the whole step, and the host time to enqueue a call
+    x, _ = hs_synth.spectrum_1d_pulsar(n_bins=131072)
+    xd = torch.from_numpy(x).cuda()
+    n_b = x.size
+    hss, outs, tile = {}, {}, {}
+    r = max(200, reps)
+    for v in VARIANTS:
+        mu, isig = hs.hs_noise_calibration(v, HMAX)
+        h = hs.HarmonicSum(variants=hs.VARIANTS[v], hmax=HMAX, max_bins=n_b, threshold=THR, cand_capacity=1 << 16,
+                           calibration={v: (mu, isig)})
+        o = h.new_outputs(n_b, v, "cuda")
+        best = None
+        for tb in (256, 512, 1024, 2048, 4096):  # tile bins of the single-spectrum launch
+            hs.hs_plan_set_tile_bins(h.plan, v, tb)
+            t = _time_ms(torch, stream, lambda: hs.hs_sum_1d(h.plan, v, xd, h.out_struct(o), h.ws, 0, stream), r)
+            if best is None or t < best[0]:
+                best = (t, tb)
+        hs.hs_plan_set_tile_bins(h.plan, v, best[1])
+        hss[v], outs[v], tile[v] = h, o, best[1]
+    per = {v: _time_ms(torch, stream, lambda v=v: hs.hs_sum_1d(hss[v].plan, v, xd, hss[v].out_struct(outs[v]),
+                                                                  hss[v].ws, 0, stream), r) for v in VARIANTS}
+
+    def step():
+        for v in VARIANTS:
+            outs[v]["cand_count"].zero_()
+            hs.hs_sum_1d(hss[v].plan, v, xd, hss[v].out_struct(outs[v]), hss[v].ws, 0, stream)
+
+    plain = _time_ms(torch, stream, step, r)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        step()
+    graph = _time_ms(torch, stream, g.replay, r)
+    stream.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(r):
+        hs.hs_sum_1d(hss["std"].plan, "std", xd, hss["std"].out_struct(outs["std"]), hss["std"].ws, 0, stream)
+    enqueue_us = (time.perf_counter() - t0) / r * 1e6
+    stream.synchronize()
+    step()
+    stream.synchronize()
+    found = {v: int(outs[v]["cand_count"].item()) for v in VARIANTS}
+    return {"workload": "one spectrum of 131072 FP32 bins, pulsar at bin 1000.37 with 16 harmonics (8/k), "
+                        "all four variants, H = 1..32, hs_sum_1d",
+            "per_variant_us": {v: per[v] * 1e3 for v in VARIANTS}, "tile_bins": tile,
+            "step_us_plain": plain * 1e3, "step_us_graph": graph * 1e3,
+            "value_graph": n_b * HMAX / (graph / 1e3), "unit": UNIT,
+            "host_enqueue_us_per_call": enqueue_us, "candidates": found}
 
 
 def main():
@@ -653,7 +827,8 @@ def main():
         n_s = min(args.cpu_sample_spectra, args.spectra)
         bins, t = cpu_oracle_sample(offsets, x_host.numpy(), n_s, variants, cores)
         line["cpu_baseline"] = {"value": bins * HMAX / t, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": "first %d spectra (%d bins), all listed variants, FP32 oracle" % (n_s, bins),
+                                "sample": "first %d spectra (%d bins), %s, FP32 oracle, each spectrum's bins split "
+                                          "across %d cores" % (n_s, bins, "+".join(variants), cores),
                                 "single_thread": cpu_single_thread(offsets, x_host.numpy(), variants)}
     if rank == 0:
         print(json.dumps(line))

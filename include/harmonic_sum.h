@@ -85,6 +85,13 @@ typedef enum hs_dtype { HS_F32 = 0, HS_F16 = 1, HS_BF16 = 2 } hs_dtype;
  * valid while H (n + 1) <= N (the furthest read is H n + H - 1).  Forward sums and adjoint;
  * calibrate with hs_noise_calibration_flags. */
 #define HS_FLAG_GREEDY_FIXED1 16
+/* Diagnostic, for testing the error path of the bounded device waits: with HS_FLAG_STAGED_SPANS,
+ * the work item holding the first tile of the batch arms its first shared-memory slot for 16 bytes
+ * more than it copies, so that slot never fills.  The consumer warps of that CTA give up after
+ * their bounded wait (about a second), the CTA stops, the launch still ends, and hs_sync_status
+ * returns HS_ERR_TIMEOUT; the outputs of that CTA's tiles are left unwritten.  No other path reads
+ * the flag. */
+#define HS_FLAG_CHECK_TIMEOUT 32
 
 typedef struct hs_plan hs_plan; /* opaque; host memory only */
 
@@ -213,7 +220,10 @@ hs_status hs_sum_batched_host(const hs_plan* plan, int variant_mask, const void*
  *   - Every call on a device shares the one array: calls that may overlap on the GPU (different
  *     streams, or different host threads) race and must be serialised by the caller.
  *   - There is no status word to read back: a candidate overflow shows as *cand_count > capacity,
- *     and a spectrum that breaks the layout contract is skipped (its outputs are not written).
+ *     a spectrum that breaks the layout contract is skipped (its outputs are not written), and a
+ *     launch whose bounded device waits gave up (only the HS_FLAG_STAGED_SPANS kernel waits) leaves
+ *     the outputs of the affected tiles unwritten.  Callers that need these signals use
+ *     hs_sum_batched and hs_sync_status.
  * Outputs, inputs and their layout are exactly those of hs_sum_batched. */
 #define HS_NOALLOC_MAX_SPECTRA 16384
 hs_status hs_sum_batched_noalloc(const hs_plan* plan, hs_variant v, const void* d_x, const int64_t* d_offsets,
@@ -224,10 +234,18 @@ hs_status hs_sum_batched_noalloc(const hs_plan* plan, hs_variant v, const void* 
 hs_status hs_sum_2d(const hs_plan* plan, const void* d_plane, int64_t n_bins, int64_t row_stride,
                     uint32_t plane_id, const hs_out2d* out, void* d_ws, size_t ws_bytes, cudaStream_t stream);
 
-/* The same plane with a chosen variant: HS_STD is hs_sum_2d; HS_FBIN is the 2-D form of Eq. 3, in
- * which the cell (n, z) is the fundamental and harmonic i reads x(i n, i z), summed in the order
- * i = 1..H, with H valid while H n <= n_bins - 1 (every H at n = 0) and H z within the plane's
- * rows.  Eq. 2 and 4 have no 2-D form in the paper: HS_ERR_UNSUPPORTED.  The plan must include v. */
+/* The same plane with a chosen variant: HS_STD is hs_sum_2d; the other three are row-wise 2-D forms
+ * of Section 2's Eq. 2-4, in which the cell (n, z) is the fundamental and harmonic i lies on the row
+ * i z, taken there as the 1-D equation takes it:
+ *   HS_FBIN    x(i n, i z)
+ *   HS_MAX     the largest of x(i n + j, i z), j = 1..i (j = 0..i under HS_FLAG_MAX_WINDOW0)
+ *   HS_GREEDY  the larger of x(i n + j, i z) and x(i n + j + 1, i z), the right one only when
+ *              strictly larger (then j grows by one); HS_FLAG_GREEDY_FIXED1 takes x(n, z) first
+ * summed in the order i = 1..H.  H is valid while the 1-D rule holds for n (H n <= n_bins - 1 for
+ * HS_FBIN, every H at n = 0; H (n + 1) <= n_bins - 1 for HS_MAX and HS_GREEDY, <= n_bins under
+ * HS_FLAG_GREEDY_FIXED1) and H z lies within the plane's rows.  The paper writes Eq. 2-4 in 1-D only;
+ * the drift i z of harmonic i follows the 2-D form of Eq. 1.  Calibrate with hs_noise_calibration
+ * (the per-row statistics are the 1-D ones).  The plan must include v. */
 hs_status hs_sum_2d_variant(const hs_plan* plan, hs_variant v, const void* d_plane, int64_t n_bins,
                             int64_t row_stride, uint32_t plane_id, const hs_out2d* out, void* d_ws, size_t ws_bytes,
                             cudaStream_t stream);

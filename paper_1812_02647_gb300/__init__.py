@@ -25,6 +25,7 @@ FLAG_STAGED_SPANS = 2
 FLAG_MAX_WINDOW0 = 4
 FLAG_POW2_STAGES = 8
 FLAG_GREEDY_FIXED1 = 16
+FLAG_CHECK_TIMEOUT = 32
 HMAX_1D, HMAX_2D = 32, 16
 
 OK, ERR_INVALID, ERR_ALIGN, ERR_CUDA, ERR_NOMEM, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, 1, 2, 3, 4, 5, 6

@@ -166,6 +166,9 @@ __device__ void st_producer(const Work1d& w, WsControl* ctl, const int64_t* pref
     item = __shfl_sync(0xffffffffu, item, 0);
     s = __shfl_sync(0xffffffffu, s, 0);
 
+    // HS_FLAG_CHECK_TIMEOUT: the item holding the batch's first tile arms its first slot for more
+    // bytes than it copies, so the consumers' bounded waits run out (tests the error path)
+    bool withhold = (w.flags & HS_FLAG_CHECK_TIMEOUT) != 0 && item == 0;
     while (ok && item < total) {
         unsigned long long next = 0;
         if (lane == 0) next = atomicAdd(&ctl->queue, 1u);  // consumed after this item's copies are queued
@@ -219,8 +222,9 @@ __device__ void st_producer(const Work1d& w, WsControl* ctl, const int64_t* pref
                         dsc.flags = direct ? kStDirect : 0u;
                         sh.desc[tile_seq % kStDescs] = dsc;
                     }
-                    mbar_arrive_expect_tx(sh.full0 + 8 * slot, tot);  // releases the descriptor store
+                    mbar_arrive_expect_tx(sh.full0 + 8 * slot, withhold ? tot + 16u : tot);  // releases the descriptor store
                 }
+                withhold = false;
                 __syncwarp();
                 if (bytes != 0u) bulk_copy_g2s(dst, src, bytes, sh.full0 + 8 * slot);
                 armed |= 1u << slot;

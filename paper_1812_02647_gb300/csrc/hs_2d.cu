@@ -264,12 +264,39 @@ __global__ void __launch_bounds__(k2dGroups * 32, 2) k_hs2d_pairs(const __grid_c
 }
 
 // ------------------------------------------------------------------------------------------
-// 2-D form of Eq. 3: the cell (n, z) is the fundamental and harmonic i reads x(i*n, i*z), added as a
-// running sum in the order i = 1..H.  H is valid while H*n <= N-1 (every H at n = 0) and H*z stays
-// within the plane's rows.  Same CTA layout and per-bin reduction as k_hs2d.
+// Row-wise 2-D forms of Eq. 2-4: harmonic i of the cell (n, z) lies on the row i*z and is taken there
+// exactly as the 1-D equation takes it: Eq. 3 x(i n, i z); Eq. 2 the largest of x(i n + j0 .. i n + i,
+// i z) (j0 = 1, or 0 under HS_FLAG_MAX_WINDOW0); Eq. 4 the choice between x(i n + j, i z) and
+// x(i n + j + 1, i z), the right one only when strictly larger, j carried from harmonic to harmonic
+// (HS_FLAG_GREEDY_FIXED1: the first term is x(n, z)).  Terms are a running sum in the order i = 1..H.
+// H is valid while the 1-D rule holds for n (Eq. 3: H n <= N-1, every H at n = 0; Eq. 2 and 4:
+// H (n+1) <= N-1, or <= N under the fixed first term) and H z stays within the plane's rows.  The
+// paper writes Eq. 2-4 in 1-D only; taking the drift of harmonic i as i z follows the 2-D form of
+// Eq. 1.  Same CTA layout and per-bin reduction as k_hs2d.
 // ------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(k2dBins * k2dGroups) k_hs2d_fbin(const __grid_constant__ Tables tb, const Work2d w,
-                                                                  const hs_out2d o, long long cand_cap, WsControl* ctl) {
+template <int V>
+__device__ __forceinline__ float rowwise_term(const float* row, uint32_t n, int i, uint32_t& j, int flags) {
+    const uint32_t base = (uint32_t)i * n;
+    if (V == HS_FBIN) return __ldg(row + base);
+    if (V == HS_MAX) {
+        const int j0 = (flags & HS_FLAG_MAX_WINDOW0) ? 0 : 1;
+        float m = __ldg(row + base + j0);
+        for (int jj = j0 + 1; jj <= i; ++jj) m = fmaxf(m, __ldg(row + base + jj));
+        return m;
+    }
+    if ((flags & HS_FLAG_GREEDY_FIXED1) && i == 1) return __ldg(row + n);
+    const float l = __ldg(row + base + j), r = __ldg(row + base + j + 1);
+    if (r > l) {
+        ++j;
+        return r;
+    }
+    return l;
+}
+
+template <int V>
+__global__ void __launch_bounds__(k2dBins * k2dGroups) k_hs2d_rowwise(const __grid_constant__ Tables tb, const Work2d w,
+                                                                     const hs_out2d o, long long cand_cap,
+                                                                     WsControl* ctl) {
     __shared__ float s_snr[k2dGroups][k2dBins];
     __shared__ int s_row[k2dGroups][k2dBins];
     __shared__ int s_h[k2dGroups][k2dBins];
@@ -278,6 +305,16 @@ __global__ void __launch_bounds__(k2dBins * k2dGroups) k_hs2d_fbin(const __grid_
     const uint32_t N = (uint32_t)w.n_bins;
     const bool active = n < N;
     const int z_max = w.z_min + w.nz - 1;
+    // valid H from the bin alone (the 1-D rule)
+    int hn = w.hmax;
+    if (active) {
+        if (V == HS_FBIN) {
+            if (n > 0) hn = min(hn, (int)((N - 1) / n));
+        } else {
+            const uint32_t L = (V == HS_GREEDY && (w.flags & HS_FLAG_GREEDY_FIXED1)) ? N : N - 1;
+            hn = min(hn, (int)(L / (n + 1)));
+        }
+    }
     float rbest = -INFINITY;
     int rrow = 0, rh = 0;
     for (int r = g; r < w.nz; r += k2dGroups) {
@@ -285,13 +322,14 @@ __global__ void __launch_bounds__(k2dBins * k2dGroups) k_hs2d_fbin(const __grid_
         float best = -INFINITY;
         int bh = 0;
         if (active) {
-            int hv = w.hmax;
-            if (n > 0) hv = min(hv, (int)((N - 1) / n));
+            int hv = hn;
             if (z > 0) hv = min(hv, z_max / z);
             if (z < 0) hv = min(hv, w.z_min / z);  // both negative: the quotient floors towards zero
             float S = 0.f;
+            uint32_t j = 0;
             for (int i = 1; i <= hv; ++i) {
-                S = __fadd_rn(S, __ldg(w.plane + (int64_t)(i * z - w.z_min) * w.row_stride + (int64_t)i * n));
+                const float* row = w.plane + (int64_t)(i * z - w.z_min) * w.row_stride;
+                S = __fadd_rn(S, rowwise_term<V>(row, n, i, j, w.flags));
                 keep_best(calibrate(tb, S, i), i, best, bh);
             }
             const size_t cell = (size_t)r * (size_t)w.n_bins + n;
@@ -305,7 +343,7 @@ __global__ void __launch_bounds__(k2dBins * k2dGroups) k_hs2d_fbin(const __grid_
         }
         if (o.cand)
             append_candidate(active && best > w.threshold, o.cand, o.cand_count, cand_cap, &ctl->status, w.plane_id,
-                             n, best, z, bh, HS_FBIN);
+                             n, best, z, bh, V);
     }
     s_snr[g][lane] = rbest;
     s_row[g][lane] = rbest == -INFINITY ? 0x7fffffff : rrow;
@@ -332,9 +370,11 @@ __global__ void __launch_bounds__(k2dBins * k2dGroups) k_hs2d_fbin(const __grid_
 cudaError_t launch_2d(hs_variant v, const Tables& tab, const Work2d& w, const hs_out2d& o, long long cand_cap,
                       WsControl* ctl, cudaStream_t s) {
     if (w.n_bins == 0) return cudaSuccess;
-    if (v == HS_FBIN) {
+    if (v != HS_STD) {
         const unsigned grid = (unsigned)((w.n_bins + k2dBins - 1) / k2dBins);
-        k_hs2d_fbin<<<grid, k2dBins * k2dGroups, 0, s>>>(tab, w, o, cand_cap, ctl);
+        if (v == HS_FBIN) k_hs2d_rowwise<HS_FBIN><<<grid, k2dBins * k2dGroups, 0, s>>>(tab, w, o, cand_cap, ctl);
+        if (v == HS_MAX) k_hs2d_rowwise<HS_MAX><<<grid, k2dBins * k2dGroups, 0, s>>>(tab, w, o, cand_cap, ctl);
+        if (v == HS_GREEDY) k_hs2d_rowwise<HS_GREEDY><<<grid, k2dBins * k2dGroups, 0, s>>>(tab, w, o, cand_cap, ctl);
         return cudaGetLastError();
     }
     // float2 stores of the cell pair (n, n+1) need an even row length and an 8-byte aligned output

@@ -19,7 +19,7 @@ using namespace hs;
 namespace {
 
 constexpr int kPlanFlags = HS_FLAG_OUT_ALL_H | HS_FLAG_STAGED_SPANS | HS_FLAG_MAX_WINDOW0 | HS_FLAG_POW2_STAGES |
-                           HS_FLAG_GREEDY_FIXED1;
+                           HS_FLAG_GREEDY_FIXED1 | HS_FLAG_CHECK_TIMEOUT;
 
 bool single_variant(int v) { return v == HS_STD || v == HS_MAX || v == HS_FBIN || v == HS_GREEDY; }
 
@@ -271,8 +271,7 @@ hs_status hs_sum_2d(const hs_plan* p, const void* d_plane, int64_t n_bins, int64
 
 hs_status hs_sum_2d_variant(const hs_plan* p, hs_variant v, const void* d_plane, int64_t n_bins, int64_t row_stride,
                             uint32_t plane_id, const hs_out2d* out, void* d_ws, size_t ws_bytes, cudaStream_t stream) {
-    if (v == HS_MAX || v == HS_GREEDY) return HS_ERR_UNSUPPORTED;
-    if (!p || p->d.nz <= 0 || (v != HS_STD && v != HS_FBIN) || !(p->d.variants & v)) return HS_ERR_INVALID;
+    if (!p || p->d.nz <= 0 || !single_variant(v) || !(p->d.variants & v)) return HS_ERR_INVALID;
     if (p->d.dtype != HS_F32) return HS_ERR_UNSUPPORTED;
     if (!d_plane || n_bins < 0 || n_bins > p->d.max_bins || row_stride < n_bins) return HS_ERR_INVALID;
     if (!aligned(d_plane, 16) || (row_stride * 4) % 16 != 0) return HS_ERR_ALIGN;
@@ -291,6 +290,7 @@ hs_status hs_sum_2d_variant(const hs_plan* p, hs_variant v, const void* d_plane,
     w.hmax = p->d.hmax;
     w.plane_id = plane_id;
     w.threshold = p->d.threshold;
+    w.flags = p->d.flags;
     return check_cuda(launch_2d(v, p->tab[vindex(v)], w, *out, p->d.cand_capacity, reinterpret_cast<WsControl*>(d_ws),
                                 stream));
 }

@@ -65,6 +65,11 @@ struct Launch {
     int opt;  // outputs per thread
 };
 
+// Zone tiling of Eq. 2-4 (hs_1d.cu): variant (0 = plain tiles), hmax, plan flags, tile parameter.
+struct ZoneSpec {
+    int v, hmax, flags, opt;
+};
+
 }  // namespace hs
 
 struct hs_plan {
@@ -110,6 +115,7 @@ struct Work2d {
     int nz, z_min, hmax;
     uint32_t plane_id;
     float threshold;
+    int flags;  // plan flags (HS_FLAG_MAX_WINDOW0, HS_FLAG_GREEDY_FIXED1 for the row-wise forms)
 };
 cudaError_t launch_2d(hs_variant v, const Tables& tab, const Work2d& w, const hs_out2d& o, long long cand_cap,
                       WsControl* ctl, cudaStream_t s);

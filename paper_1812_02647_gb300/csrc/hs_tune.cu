@@ -91,7 +91,7 @@ extern "C" hs_status hs_autotune(hs_plan* p, hs_variant v, int64_t n_bins, void*
     o.path = reinterpret_cast<uint32_t*>(base + xr_b + o4_b);
     o.best_h = reinterpret_cast<uint8_t*>(base + xr_b + 2 * o4_b);
     const int old_opt = p->launch[vindex(v)].opt;
-    const int choices[] = {2, 4, 8, 16, 32};
+    const int choices[] = {2, 4, 8, 16, 32, 64};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HS_ERR_CUDA;
     float best_ms = 1e30f;
@@ -135,7 +135,7 @@ extern "C" hs_status hs_autotune_batched(hs_plan* p, hs_variant v, const void* d
     o.cand = nullptr;  // timing runs do not touch the caller's candidate list
     o.cand_count = nullptr;
     const int old_opt = p->launch[vindex(v)].opt;
-    const int choices[] = {2, 4, 8, 16, 32};
+    const int choices[] = {2, 4, 8, 16, 32, 64};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return HS_ERR_CUDA;
     float best_ms = 1e30f;

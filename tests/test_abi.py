@@ -34,6 +34,19 @@ def test_library_exports_every_declared_symbol(hs_lib):
     assert not missing, missing
 
 
+def header_defines():
+    return {m.group(1): m.group(2) for m in re.finditer(r"#define\s+(HS_[A-Z0-9_]+)\s+(\S+)", open(HEADER).read())}
+
+
+def test_binding_constants_match_the_header(hs_lib):
+    """The Python binding restates some header constants; they must not drift apart."""
+    d = header_defines()
+    assert int(d["HS_NOALLOC_MAX_SPECTRA"]) == hs_lib.NOALLOC_MAX_SPECTRA
+    assert int(d["HS_HMAX_1D"]) == hs_lib.HMAX_1D and int(d["HS_HMAX_2D"]) == hs_lib.HMAX_2D
+    for name in ("OUT_ALL_H", "STAGED_SPANS", "MAX_WINDOW0", "POW2_STAGES", "GREEDY_FIXED1", "CHECK_TIMEOUT"):
+        assert int(d["HS_FLAG_" + name]) == getattr(hs_lib, "FLAG_" + name), name
+
+
 def test_status_strings(hs_lib):
     for s in (0, 1, 2, 3, 4, 5, 6, 100):
         assert hs_lib.hs_status_string(s).startswith("HS_")
@@ -43,7 +56,7 @@ def test_status_strings(hs_lib):
 @pytest.mark.parametrize("bad", [dict(variants=0), dict(variants=16), dict(hmax=0), dict(hmax=33),
                                  dict(dtype=3), dict(max_bins=-1), dict(max_bins=(1 << 26) + 1),
                                  dict(nz=5, z_min=1, hmax=16), dict(nz=5, z_min=-5, hmax=16),
-                                 dict(nz=5, z_min=-2, hmax=17), dict(cand_capacity=-1), dict(flags=32),
+                                 dict(nz=5, z_min=-2, hmax=17), dict(cand_capacity=-1), dict(flags=64),
                                  dict(nz=5, z_min=-2, hmax=16, flags=8),
                                  dict(threshold=float("nan"))])
 def test_plan_create_rejects(hs_lib, bad):

@@ -103,7 +103,8 @@ def test_1d_ragged_sizes_bit_exact(hs_lib, torch, variant, n_bins):
 @pytest.mark.parametrize("n_bins", [2, 31, 33, 100, 257, 1000, 4097, 8191, 65536 + 13, 300001, 1 << 20])
 def test_1d_fast_paths_bit_exact(hs_lib, torch, variant, n_bins):
     """Without the every-H table the kernels take their fast paths (Eq. 1 output pairs, Eq. 2
-    warp-cooperative windows); they must still equal the oracle bit for bit."""
+    harmonics 1-4 by plain loads and longer windows by aligned 16-byte chunks); they must still
+    equal the oracle bit for bit."""
     x = hs_synth.spectrum(79, n_bins, n_bins, pulsar=dict(shape=1, n_harm=20, f0=n_bins / 97.3, amp=9.0, width=1.5))
     hs, mu, isig = _make(hs_lib, variant, True, flags=0)
     o = hs.sum_1d(variant, torch.from_numpy(x).cuda())
@@ -793,10 +794,39 @@ def test_2d_fbin_bit_exact(hs_lib, torch, nz, z_min, nb):
     np.testing.assert_array_equal(got, exp)
     s = hs_lib.Out2d(o["best_snr"].data_ptr(), o["best_h"].data_ptr(), o["best_snr_n"].data_ptr(),
                      o["best_h_n"].data_ptr(), o["best_z_n"].data_ptr(), None, None)
-    for v in ("max", "greedy"):  # no 2-D form in the paper
+    for v in ("max", "greedy"):  # not in this plan
         with pytest.raises(hs_lib.HSError) as e:
             hs_lib.hs_sum_2d(hs.plan, plane, s, hs.ws, variant=v)
-        assert e.value.status == hs_lib.ERR_UNSUPPORTED
+        assert e.value.status == hs_lib.ERR_INVALID
+
+
+@pytest.mark.parametrize("variant,flag,ovariant", [("max", None, "max"), ("max", "FLAG_MAX_WINDOW0", "max0"),
+                                                   ("greedy", None, "greedy"),
+                                                   ("greedy", "FLAG_GREEDY_FIXED1", "greedy1")])
+@pytest.mark.parametrize("nz,z_min,nb,hmax", [(11, -5, 3001, 16), (7, -3, 4096, 16), (1, 0, 1000, 16),
+                                              (9, -8, 257, 5), (31, -15, 64, 16)])
+def test_2d_rowwise_max_greedy_bit_exact(hs_lib, torch, variant, flag, ovariant, nz, z_min, nb, hmax):
+    """The row-wise 2-D forms of Eq. 2 and 4 (harmonic i on row i z) against the oracle, calibrated,
+    with candidates, on planes whose drift range cuts the valid H at both ends."""
+    stride = (nb + 3) // 4 * 4
+    full = np.stack([hs_synth.spectrum(124, r, stride) for r in range(nz)]).astype(np.float32)
+    plane = torch.from_numpy(full).cuda()[:, :nb]
+    flags = getattr(hs_lib, flag) if flag else 0
+    hs = hs_lib.HarmonicSum(variants=hs_lib.VARIANTS[variant], hmax=hmax, nz=nz, z_min=z_min, max_bins=stride,
+                            threshold=THR, cand_capacity=1 << 16, flags=flags)
+    mu, isig = hs_lib.hs_noise_calibration(variant, hmax, flags=flags)
+    hs.set_calibration(variant, mu, isig)
+    o = hs.sum_2d(plane, plane_id=9, variant=variant)
+    assert hs.sync_status() == hs_lib.OK
+    r = oracle.hs_2d(full[:, :nb], z_min, hmax=hmax, mu=mu, isig=isig, variant=ovariant, nthreads=8)
+    for k in ("best_snr", "best_h", "best_snr_n", "best_h_n"):
+        np.testing.assert_array_equal(o[k].cpu().numpy(), r[k], err_msg=k)
+    np.testing.assert_array_equal(o["best_z_n"].cpu().numpy().astype(np.int32), r["best_z_n"])
+    c = hs_lib.read_candidates(o)
+    exp = np.nonzero(r["best_snr"].ravel() > THR)[0]
+    assert c.size == exp.size and (c["variant"] == hs_lib.VARIANTS[variant]).all() and (c["spectrum"] == 9).all()
+    got = np.sort((c["z"].astype(np.int64) - z_min) * nb + c["bin"].astype(np.int64))
+    np.testing.assert_array_equal(got, exp)
 
 
 @pytest.mark.parametrize("variant,flag,ovariant", [("max", "FLAG_MAX_WINDOW0", "max0"),

@@ -47,6 +47,34 @@ def test_noalloc_matches_workspace_entry_point(hs_lib):
             np.testing.assert_array_equal(a, b)
 
 
+def test_noalloc_staged_spans_matches_workspace_entry_point(hs_lib):
+    """Eq. 1 through the staged-span kernel (HS_FLAG_STAGED_SPANS), the one path with bounded
+    device waits and its own tile size over the same prefix array."""
+    import torch
+
+    lens = [4096, 100000, 0, 65536, 8, 250000, 16, 131072, 1 << 20]
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    x = hs_synth.batch(304, offsets)
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda()
+    hs = hs_lib.HarmonicSum(variants=hs_lib.STD, threshold=6.0, cand_capacity=1 << 16, max_spectra=len(lens),
+                            flags=hs_lib.FLAG_STAGED_SPANS)
+    mu, isig = hs_lib.hs_noise_calibration("std", 32)
+    hs.set_calibration("std", mu, isig)
+    for tile_bins in (1024, 8192):
+        hs_lib.hs_plan_set_tile_bins(hs.plan, "std", tile_bins)
+        ref = hs.sum_batched("std", xd, od, first_id=3)
+        assert hs.sync_status() == hs_lib.OK
+        for call in range(2):
+            o = hs.new_outputs(x.size, "std", "cuda")
+            o["best_snr"].fill_(-5.0)
+            hs_lib.hs_sum_batched_noalloc(hs.plan, "std", xd, od, hs.out_struct(o), first_id=3)
+            torch.cuda.synchronize()
+            assert torch.equal(o["best_snr"], ref["best_snr"]), (tile_bins, call)
+            assert torch.equal(o["best_h"], ref["best_h"]), (tile_bins, call)
+            assert int(o["cand_count"].item()) == int(ref["cand_count"].item())
+
+
 def test_noalloc_rejects_batches_beyond_its_scratch(hs_lib):
     import torch
 
