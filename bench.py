@@ -71,6 +71,19 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def measure_l2_copy_gbs(torch, stream, mib=24, reps=200):
+    """L2-resident copy rate (read + write bytes / time): two buffers of `mib` MiB, far below the L2
+    capacity, copied back and forth; the L2 counterpart of the HBM copy figure."""
+    n = mib * (1 << 20) // 4
+    a = torch.ones(n, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    ms = _time_ms(torch, stream, lambda: b.copy_(a), reps)
+    del a, b
+    return 2 * n * 4 / (ms / 1e3) / 1e9
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -769,23 +782,36 @@ def main():
     def compulsory_bytes(v):
         return total * (4 + 4 + 1 + (4 if v == "greedy" else 0))
 
+    # ncu figures per kernel (DRAM bytes and L2-to-L1 read bytes per bin, from a capture of the same
+    # sources; null once a source file differs from the one captured)
+    prof = {}
+    try:
+        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        if tj.get("csrc_sha16") == csrc_sha16() and not args.staged_spans:
+            prof = tj.get("kernels", {})
+    except Exception:
+        pass
+    with torch.cuda.stream(stream):
+        l2_peak = measure_l2_copy_gbs(torch, stream)
     per_roof = {}
     for v in variants:
         gbs = compulsory_bytes(v) / (avg[v] / 1e3) / 1e9
-        per_roof[v] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
-    traffic = None
-    binding = None
-    try:
-        tj = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        if tj.get("csrc_sha16") == csrc_sha16() and dom == "std" and not args.staged_spans:
-            traffic = tj["dram_bytes_per_bin"] * total
-            binding = tj.get("ncu_pct")
-    except Exception:
-        pass
+        per_roof[v] = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                       "kernel": prof.get(v, {}).get("kernel")}
+        if v in prof:
+            l2b = prof[v]["l2_read_bytes_per_bin"] * total
+            per_roof[v]["l2"] = {"bytes_per_launch": l2b, "bytes_per_bin": prof[v]["l2_read_bytes_per_bin"],
+                                 "achieved": l2b / (avg[v] / 1e3) / 1e9, "peak": l2_peak, "unit": "GB/s",
+                                 "frac": l2b / (avg[v] / 1e3) / 1e9 / l2_peak,
+                                 "peak_source": "measured in this run: L2-resident 24 MiB copy"}
+            per_roof[v]["traffic"] = prof[v]["dram_bytes_per_bin"] * total
+            per_roof[v]["ncu_pct_of_peak"] = prof[v].get("ncu_pct")
+    traffic = prof["std"]["dram_bytes_per_bin"] * total if "std" in prof else None
+    binding = prof["std"].get("ncu_pct") if "std" in prof else None
     if dom == "std":
         # Eq. 1 performs 528 ordered FP32 adds per bin (sum_{H<=32} H); its HBM bytes are negligible
         tf = 528.0 * total / (avg[dom] / 1e3) / 1e12
-        kname = "hs::k_hs1d_eq1_staged" if args.staged_spans else "hs::k_hs1d_batched<Eq. 1>"
+        kname = "hs::k_hs1d_eq1_staged" if args.staged_spans else "hs::k_eq1_pairs_batched<float, false>"
         roof = {"bound": "alu", "kernel": kname, "achieved": tf, "peak": alu_peak,
                 "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock", "unit": "TFLOP/s",
                 "frac": tf / alu_peak, "traffic": traffic, "algorithmic_flops_per_launch": 528.0 * total}
@@ -793,8 +819,8 @@ def main():
             roof["ncu_pct_of_peak"] = binding
     else:
         r = per_roof[dom]
-        roof = {**r, "kernel": "hs::k_hs1d_batched<%s>" % dom, "peak_source": peak_src, "traffic": None,
-                "algorithmic_bytes_per_launch": compulsory_bytes(dom)}
+        roof = {**r, "kernel": "hs::k_hs1d_zoned<%s>" % dom, "peak_source": peak_src,
+                "traffic": r.get("traffic"), "algorithmic_bytes_per_launch": compulsory_bytes(dom)}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",

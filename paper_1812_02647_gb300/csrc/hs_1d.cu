@@ -339,6 +339,42 @@ struct Bin<HS_GREEDY, T> {
             for (int i = hv + 1; i <= hmax; ++i) all_h[(size_t)(i - 1) * all_stride + n] = -INFINITY;
         path = p;
     }
+    // Two bins of the same valid count, their chains interleaved: the reads of one bin's next harmonic
+    // wait on that bin's choice only, so two chains keep twice the loads in flight.  No every-H table.
+    template <bool P2>
+    static __device__ __forceinline__ void eval2(const T* x, uint32_t n1, uint32_t n2, int hv, const Tables& tb,
+                                                 float& b1, int& h1, uint32_t& path1, float& b2, int& h2,
+                                                 uint32_t& path2, uint32_t flags) {
+        const bool fixed1 = (flags & HS_FLAG_GREEDY_FIXED1) != 0;
+        float S1 = 0.f, S2 = 0.f;
+        uint32_t j1 = 0, j2 = 0, q1 = 0, q2 = 0;
+#pragma unroll
+        for (int i = 1; i <= kHmax; ++i) {
+            if (i > hv) break;
+            if (fixed1 && i == 1) {
+                S1 = __fadd_rn(S1, ldx(x, n1));
+                S2 = __fadd_rn(S2, ldx(x, n2));
+            } else {
+                const T* a = x + ((uint32_t)i * n1 + j1);
+                const T* b = x + ((uint32_t)i * n2 + j2);
+                const float l1 = widen<T>(__ldg(a)), r1 = widen<T>(__ldg(a + 1));
+                const float l2 = widen<T>(__ldg(b)), r2 = widen<T>(__ldg(b + 1));
+                const bool g1 = r1 > l1, g2 = r2 > l2;
+                q1 |= (g1 ? 1u : 0u) << (i - 1);
+                q2 |= (g2 ? 1u : 0u) << (i - 1);
+                j1 += g1 ? 1u : 0u;
+                j2 += g2 ? 1u : 0u;
+                S1 = __fadd_rn(S1, g1 ? r1 : l1);
+                S2 = __fadd_rn(S2, g2 ? r2 : l2);
+            }
+            if (!P2 || is_pow2(i)) {
+                keep_best(calibrate(tb, S1, i), i, b1, h1);
+                keep_best(calibrate(tb, S2, i), i, b2, h2);
+            }
+        }
+        path1 = q1;
+        path2 = q2;
+    }
 };
 
 // ------------------------------------------------------------------------------------------
@@ -561,6 +597,35 @@ __device__ __forceinline__ void zone_run(const T* x, uint32_t N, uint32_t lo, ui
                                          const Work1d& w, const Out1d& o, size_t out_off, uint32_t spec,
                                          unsigned* status) {
     const int hv = H > 0 ? H : h;
+    if constexpr (V == HS_GREEDY && H != 1) {
+        // Eq. 4: thread t takes the bins base + t and base + kBlock + t together
+        for (uint32_t base = lo; base < hi; base += 2 * kBlock) {
+            const uint32_t n1 = base + threadIdx.x, n2 = n1 + kBlock;
+            const bool a1 = n1 < hi, a2 = n2 < hi;
+            float b1 = -INFINITY, b2 = -INFINITY;
+            int h1 = 0, h2 = 0;
+            uint32_t p1 = 0, p2 = 0;
+            if (a1) {
+                Bin<V, T>::template eval2<P2>(x, n1, a2 ? n2 : n1, hv, tb, b1, h1, p1, b2, h2, p2,
+                                              (uint32_t)w.flags);
+                o.best_snr[out_off + n1] = b1;
+                o.best_h[out_off + n1] = (uint8_t)h1;
+                if (o.path) o.path[out_off + n1] = p1;
+            }
+            if (a2) {
+                o.best_snr[out_off + n2] = b2;
+                o.best_h[out_off + n2] = (uint8_t)h2;
+                if (o.path) o.path[out_off + n2] = p2;
+            }
+            if (o.cand) {
+                append_candidate(a1 && b1 > w.threshold, o.cand, o.cand_count, o.cand_cap, status, spec, n1, b1, 0,
+                                 h1, V);
+                append_candidate(a2 && b2 > w.threshold, o.cand, o.cand_count, o.cand_cap, status, spec, n2, b2, 0,
+                                 h2, V);
+            }
+        }
+        return;
+    }
     // zone 1 also holds the bins with no valid H at all (from edge(1) on): they keep -inf, 0
     const uint32_t e1 = H == 1 ? zone_edge(V, N, zone_limit(V, N, w.flags), 1) : 0u;
     for (uint32_t base = lo; base < hi; base += kBlock) {
@@ -850,8 +915,8 @@ void launch_tile_scan(const int64_t* offsets, int n_spectra, int64_t tile, int64
 
 template <int V, typename T, bool P2>
 static int& occupancy_slot() {
-    static int occ = 0;  // resident CTAs per SM of the persistent kernel
-    return occ;
+    static int occ[kMaxDevices] = {};  // resident CTAs per SM of the persistent kernel, per device
+    return occ[device_slot()];
 }
 
 template <int V, typename T, bool P2>
@@ -866,8 +931,8 @@ static int occupancy() {
 
 template <int V, typename T, bool P2>
 static int& zoned_occupancy_slot() {
-    static int occ = 0;  // resident CTAs per SM of the persistent zoned kernel
-    return occ;
+    static int occ[kMaxDevices] = {};  // resident CTAs per SM of the persistent zoned kernel, per device
+    return occ[device_slot()];
 }
 
 template <int V, typename T, bool P2>
@@ -891,15 +956,15 @@ static cudaError_t launch_zoned(const Tables& tab, const Work1d& w, const Out1d&
         return cudaGetLastError();
     }
     k_tile_scan<<<1, 1024, 0, s>>>(w.offsets, w.n_spectra, 0, w.max_bins, (int)sizeof(T), z, prefix, ctl);
-    k_hs1d_zoned<V, T, P2><<<(unsigned)(sm_count * zoned_occupancy<V, T, P2>()), kBlock, 0, s>>>(tab, w, o, ctl,
-                                                                                              prefix);
+    const int occ = zoned_occupancy<V, T, P2>();
+    k_hs1d_zoned<V, T, P2><<<(unsigned)(sm_count * occ), kBlock, 0, s>>>(tab, w, o, ctl, prefix);
     return cudaGetLastError();
 }
 
 template <typename T, bool P2>
 static int& pair_occupancy_slot() {
-    static int occ = 0;  // resident CTAs per SM of the persistent Eq. 1 pair kernel
-    return occ;
+    static int occ[kMaxDevices] = {};  // resident CTAs per SM of the persistent Eq. 1 pair kernel, per device
+    return occ[device_slot()];
 }
 
 template <typename T, bool P2>

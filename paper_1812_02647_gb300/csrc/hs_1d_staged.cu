@@ -436,9 +436,16 @@ __global__ void __launch_bounds__(kStThreads, kStCtas)
 
 template <typename T>
 cudaError_t set_smem_attr() {
-    static cudaError_t e = cudaFuncSetAttribute(k_hs1d_eq1_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                (int)kStSmemBytes);
-    return e;
+    // the attribute belongs to the device context: set once per device
+    static bool done[kMaxDevices] = {};
+    static cudaError_t err[kMaxDevices] = {};
+    const int d = device_slot();
+    if (!done[d]) {
+        err[d] = cudaFuncSetAttribute(k_hs1d_eq1_staged<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kStSmemBytes);
+        done[d] = true;
+    }
+    return err[d];
 }
 
 template <typename T>

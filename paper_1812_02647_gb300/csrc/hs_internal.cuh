@@ -65,6 +65,15 @@ struct Launch {
     int opt;  // outputs per thread
 };
 
+// Values worth computing once per device (occupancies, function attributes): slot d of an array of
+// kMaxDevices belongs to device ordinal d.  A device ordinal beyond the table shares slot 0.
+constexpr int kMaxDevices = 64;
+inline int device_slot() {
+    int d = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) d = 0;
+    return d;
+}
+
 // Zone tiling of Eq. 2-4 (hs_1d.cu): variant (0 = plain tiles), hmax, plan flags, tile parameter.
 struct ZoneSpec {
     int v, hmax, flags, opt;

@@ -24,7 +24,6 @@ constexpr size_t kNoallocBytes = (kWsControlBytes + sizeof(int64_t) * (size_t)(k
 // One copy per device that loads the library; it lives until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 
-constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
