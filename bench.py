@@ -72,14 +72,15 @@ def load_peaks():
 
 
 def measure_l2_copy_gbs(torch, stream, mib=24, reps=200):
-    """L2-resident copy rate (read + write bytes / time): two buffers of `mib` MiB, far below the L2
-    capacity, copied back and forth; the L2 counterpart of the HBM copy figure."""
+    """L2-resident copy rate through the SMs (read + write bytes / time): an elementwise kernel that
+    reads one buffer of `mib` MiB and writes another, both far below the L2 capacity; the L2
+    counterpart of the HBM copy figure (a device-to-device memcpy would not run on the SMs)."""
     n = mib * (1 << 20) // 4
     a = torch.ones(n, device="cuda")
     b = torch.empty_like(a)
     for _ in range(10):
-        b.copy_(a)
-    ms = _time_ms(torch, stream, lambda: b.copy_(a), reps)
+        torch.mul(a, 2.0, out=b)
+    ms = _time_ms(torch, stream, lambda: torch.mul(a, 2.0, out=b), reps)
     del a, b
     return 2 * n * 4 / (ms / 1e3) / 1e9
 
@@ -803,7 +804,7 @@ def main():
             per_roof[v]["l2"] = {"bytes_per_launch": l2b, "bytes_per_bin": prof[v]["l2_read_bytes_per_bin"],
                                  "achieved": l2b / (avg[v] / 1e3) / 1e9, "peak": l2_peak, "unit": "GB/s",
                                  "frac": l2b / (avg[v] / 1e3) / 1e9 / l2_peak,
-                                 "peak_source": "measured in this run: L2-resident 24 MiB copy"}
+                                 "peak_source": "measured in this run: L2-resident 24 MiB elementwise copy"}
             per_roof[v]["traffic"] = prof[v]["dram_bytes_per_bin"] * total
             per_roof[v]["ncu_pct_of_peak"] = prof[v].get("ncu_pct")
     traffic = prof["std"]["dram_bytes_per_bin"] * total if "std" in prof else None
