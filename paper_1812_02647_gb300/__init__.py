@@ -20,6 +20,7 @@ STD, MAX, FBIN, GREEDY = 1, 2, 4, 8
 VARIANTS = {"std": STD, "max": MAX, "fbin": FBIN, "greedy": GREEDY}
 VARIANT_NAMES = {v: k for k, v in VARIANTS.items()}
 F32, F16, BF16 = 0, 1, 2
+DTYPE_NAMES = {F32: "f32", F16: "f16", BF16: "bf16"}
 FLAG_OUT_ALL_H = 1
 FLAG_STAGED_SPANS = 2
 FLAG_MAX_WINDOW0 = 4
@@ -126,6 +127,38 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
+# Storage type of each live plan, by handle.  The C calls take the spectra as a bare pointer and read
+# them as the plan's type, so a tensor of another type would be read past its end.
+_plan_dtype = {}
+
+
+def _spectra(plan, x, rows=False):
+    """Pointer to input spectra after checking them against the plan: the plan's storage type and
+    contiguous elements (contiguous rows for a 2-D plane, whose row stride is passed separately);
+    a mismatch is an error, not a read of the wrong bytes."""
+    want = _plan_dtype.get(getattr(plan, "value", None))
+    try:
+        got = _dtype_code(x.dtype)
+    except KeyError:
+        got = None
+    dense = x.stride(-1) == 1 if rows else x.is_contiguous()
+    if (want is not None and got != want) or not dense:
+        raise HSError(ERR_INVALID, "input spectra (%s%s) do not match the plan's storage type %s"
+                      % (x.dtype, "" if dense else ", not contiguous", DTYPE_NAMES.get(want, want)))
+    return _ptr(x)
+
+
+def _offsets(offsets):
+    """Pointer to a batch's int64 spectrum offsets (checked: another integer type would be misread)."""
+    import torch
+
+    if offsets is None:
+        return None
+    if offsets.dtype != torch.int64 or not offsets.is_contiguous():
+        raise HSError(ERR_INVALID, "spectrum offsets must be a contiguous int64 tensor, got %s" % offsets.dtype)
+    return _ptr(offsets)
+
+
 def _stream(stream=None):
     import torch
 
@@ -143,10 +176,12 @@ def hs_plan_create(variants=0xF, hmax=32, dtype=F32, max_bins=1 << 22, nz=0, z_m
                  int(cand_capacity), int(flags))
     h = _P()
     _check(_lib.hs_plan_create(ctypes.byref(h), ctypes.byref(d)), "hs_plan_create")
+    _plan_dtype[h.value] = int(dtype)
     return h, d
 
 
 def hs_plan_destroy(plan):
+    _plan_dtype.pop(getattr(plan, "value", None), None)
     return _lib.hs_plan_destroy(plan)
 
 
@@ -186,29 +221,32 @@ def _out(best_snr, best_h, path=None, all_h=None, cand=None, cand_count=None):
 
 
 def hs_sum_1d(plan, variant, x, out: Out, ws, spectrum_id=0, stream=None):
-    return _check(_lib.hs_sum_1d(plan, _variant(variant), _ptr(x), x.numel(), spectrum_id, ctypes.byref(out),
-                                 _ptr(ws), ws.numel(), _stream(stream)), "hs_sum_1d")
+    return _check(_lib.hs_sum_1d(plan, _variant(variant), _spectra(plan, x), x.numel(), spectrum_id,
+                                 ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)), "hs_sum_1d")
 
 
 def hs_sum_batched(plan, variant, x, offsets, out: Out, ws, first_id=0, stream=None):
-    return _check(_lib.hs_sum_batched(plan, _variant(variant), _ptr(x), _ptr(offsets), offsets.numel() - 1, first_id,
-                                      ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)), "hs_sum_batched")
+    return _check(_lib.hs_sum_batched(plan, _variant(variant), _spectra(plan, x), _offsets(offsets),
+                                      offsets.numel() - 1, first_id, ctypes.byref(out), _ptr(ws), ws.numel(),
+                                      _stream(stream)), "hs_sum_batched")
 
 
 def hs_sum_2d(plan, plane, out: Out2d, ws, plane_id=0, stream=None, variant="std"):
     """2-D sums over a (nz, n_bins) plane: Eq. 1 ("std") or its freq-bin form ("fbin")."""
     nz, nb = plane.shape
+    p = _spectra(plan, plane, rows=True)
     if _variant(variant) == STD:
-        return _check(_lib.hs_sum_2d(plan, _ptr(plane), nb, plane.stride(0), plane_id, ctypes.byref(out), _ptr(ws),
+        return _check(_lib.hs_sum_2d(plan, p, nb, plane.stride(0), plane_id, ctypes.byref(out), _ptr(ws),
                                      ws.numel(), _stream(stream)), "hs_sum_2d")
-    return _check(_lib.hs_sum_2d_variant(plan, _variant(variant), _ptr(plane), nb, plane.stride(0), plane_id,
+    return _check(_lib.hs_sum_2d_variant(plan, _variant(variant), p, nb, plane.stride(0), plane_id,
                                          ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)), "hs_sum_2d_variant")
 
 
 def hs_backward(plan, variant, x, offsets, grad_snr, best_h, path, grad_x, stream=None):
     n_spec = 1 if offsets is None else offsets.numel() - 1
-    return _check(_lib.hs_backward(plan, _variant(variant), _ptr(x), _ptr(offsets), n_spec, x.numel(), _ptr(grad_snr),
-                                   _ptr(best_h), _ptr(path), _ptr(grad_x), _stream(stream)), "hs_backward")
+    return _check(_lib.hs_backward(plan, _variant(variant), _spectra(plan, x), _offsets(offsets), n_spec, x.numel(),
+                                   _ptr(grad_snr), _ptr(best_h), _ptr(path), _ptr(grad_x), _stream(stream)),
+                  "hs_backward")
 
 
 def hs_standardize_cast(p, offsets, mu, sigma, dst_dtype, out, stream=None):
@@ -249,9 +287,9 @@ def hs_sift_candidates(cand, cand_count, out, out_count, tmp, ws, tol_bins=1.5, 
 def hs_graph_create_batched(plan, variant_mask, x, offsets, outs, ws, first_id=0, stream=None):
     arr = (Out * len(outs))(*outs)
     g = _P()
-    _check(_lib.hs_graph_create_batched(plan, int(variant_mask), _ptr(x), _ptr(offsets), offsets.numel() - 1,
-                                        first_id, ctypes.cast(arr, _P), _ptr(ws), ws.numel(), _stream(stream),
-                                        ctypes.byref(g)), "hs_graph_create_batched")
+    _check(_lib.hs_graph_create_batched(plan, int(variant_mask), _spectra(plan, x), _offsets(offsets),
+                                        offsets.numel() - 1, first_id, ctypes.cast(arr, _P), _ptr(ws), ws.numel(),
+                                        _stream(stream), ctypes.byref(g)), "hs_graph_create_batched")
     return g
 
 
@@ -261,8 +299,9 @@ def hs_sum_batched_host(plan, variant_mask, x_host, offsets_host, x_dev, offsets
     ``x_host`` is a pinned torch tensor, ``offsets_host`` a numpy int64 array (starting at 0)."""
     offs = np.ascontiguousarray(offsets_host, dtype=np.int64)
     arr = (Out * len(outs))(*outs)
-    return _check(_lib.hs_sum_batched_host(plan, int(variant_mask), ctypes.c_void_p(x_host.data_ptr()),
-                                           offs.ctypes.data, len(offs) - 1, first_id, _ptr(x_dev), _ptr(offsets_dev),
+    return _check(_lib.hs_sum_batched_host(plan, int(variant_mask), _spectra(plan, x_host),
+                                           offs.ctypes.data, len(offs) - 1, first_id, _spectra(plan, x_dev),
+                                           _offsets(offsets_dev),
                                            ctypes.cast(arr, _P), int(n_chunks), _ptr(ws), ws.numel(),
                                            _stream(stream)), "hs_sum_batched_host")
 
@@ -281,9 +320,9 @@ def hs_autotune(plan, variant, n_bins, scratch, ws, stream=None):
 
 
 def hs_autotune_batched(plan, variant, x, offsets, out: Out, ws, stream=None):
-    return _check(_lib.hs_autotune_batched(plan, _variant(variant), _ptr(x), _ptr(offsets), offsets.numel() - 1,
-                                           ctypes.byref(out), _ptr(ws), ws.numel(), _stream(stream)),
-                  "hs_autotune_batched")
+    return _check(_lib.hs_autotune_batched(plan, _variant(variant), _spectra(plan, x), _offsets(offsets),
+                                           offsets.numel() - 1, ctypes.byref(out), _ptr(ws), ws.numel(),
+                                           _stream(stream)), "hs_autotune_batched")
 
 
 def hs_plan_tile_bins(plan, variant) -> int:
@@ -462,5 +501,6 @@ _lib.hs_sum_batched_noalloc.restype = ctypes.c_int
 def hs_sum_batched_noalloc(plan, variant, x, offsets, out: Out, first_id=0, stream=None):
     """hs_sum_batched without a workspace, for callers that may not allocate device memory while
     they run (the library's own fixed scratch array is used; see include/harmonic_sum.h)."""
-    return _check(_lib.hs_sum_batched_noalloc(plan, _variant(variant), _ptr(x), _ptr(offsets), offsets.numel() - 1,
-                                              first_id, ctypes.byref(out), _stream(stream)), "hs_sum_batched_noalloc")
+    return _check(_lib.hs_sum_batched_noalloc(plan, _variant(variant), _spectra(plan, x), _offsets(offsets),
+                                              offsets.numel() - 1, first_id, ctypes.byref(out), _stream(stream)),
+                  "hs_sum_batched_noalloc")

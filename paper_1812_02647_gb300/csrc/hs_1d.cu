@@ -35,23 +35,6 @@ struct Bin;
 // fractions.  Each pass reduces its own H with the first-largest rule and the passes merge with
 // "larger snr, or equal snr and smaller H", which gives the same best H as one scan over H = 1..32.
 // ------------------------------------------------------------------------------------------
-__host__ __device__ constexpr bool in_hset(uint32_t M, int H) { return H >= 1 && H <= 32 && ((M >> (H - 1)) & 1u); }
-__host__ __device__ constexpr int hslot(uint32_t M, int H) {  // position of H among the set's members
-    int s = 0;
-    for (int h = 1; h < H; ++h) s += in_hset(M, h) ? 1 : 0;
-    return s;
-}
-__host__ __device__ constexpr int hset_size(uint32_t M) { return hslot(M, 33); }
-__host__ __device__ constexpr bool frac_in_hset(uint32_t M, int q) {
-    for (int m = 1; m * q <= 32; ++m)
-        if (in_hset(M, m * q)) return true;
-    return false;
-}
-__host__ __device__ constexpr uint32_t hset(std::initializer_list<int> hs) {
-    uint32_t m = 0;
-    for (int h : hs) m |= 1u << (h - 1);
-    return m;
-}
 constexpr uint32_t kEq1Pass0 = hset({3, 5, 7, 10, 14, 15, 20, 21, 25, 28, 30});
 constexpr uint32_t kEq1Pass1 = hset({4, 6, 8, 9, 12, 16, 18, 24, 27, 29, 32});
 constexpr uint32_t kEq1Pass2 = hset({1, 2, 11, 13, 17, 19, 22, 23, 26, 31});
@@ -112,12 +95,6 @@ template <uint32_t M, int... Hs>
 __device__ __forceinline__ void pair_keep_all(const Tables& tb, const float2* S, float& pa, int& qa, float& pb,
                                               int& qb, std::integer_sequence<int, Hs...>) {
     (pair_keep<M, Hs + 1>(tb, S, pa, qa, pb, qb), ...);
-}
-__device__ __forceinline__ void merge_best(float p, int q, float& best, int& bh) {
-    if (p > best || (p == best && q < bh)) {
-        best = p;
-        bh = q;
-    }
 }
 template <typename T, uint32_t M, int... K>
 __device__ __forceinline__ void pair_pass(const T* x, uint32_t n, const Tables& tb, float& ba, int& ha, float& bb,

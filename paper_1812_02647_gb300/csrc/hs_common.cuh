@@ -58,6 +58,15 @@ __device__ __forceinline__ void keep_best(float snr, int H, float& best, int& bh
     }
 }
 
+// Merge of two first-largest reductions over disjoint sets of H: the larger snr, or on equal snr the
+// smaller H, which is what one scan over H = 1, 2, .. with strict > would keep.
+__device__ __forceinline__ void merge_best(float p, int q, float& best, int& bh) {
+    if (p > best || (p == best && q < bh)) {
+        best = p;
+        bh = q;
+    }
+}
+
 // Warp-aggregated append of at most one candidate per lane.  Must be reached by all 32 lanes.
 __device__ __forceinline__ void append_candidate(bool hit, hs_candidate* cand, unsigned long long* count,
                                                  long long cap, unsigned* status, uint32_t spec, uint32_t bin,

@@ -2,6 +2,7 @@
 // 1-D kernels.
 #pragma once
 
+#include <initializer_list>
 #include <utility>
 
 #include "hs_common.cuh"
@@ -66,6 +67,27 @@ template <typename T, bool P2 = false, int... K>
 __device__ __forceinline__ void farey_all(const T* x, uint32_t n, int hmax, float (&S)[kHmax + 1],
                                           std::integer_sequence<int, K...>) {
     (farey_step<T, K, P2>(x, n, hmax, S), ...);  // in increasing fraction order
+}
+
+
+// Sets of H as bit masks (bit H-1), for sweeps that keep only some of the sums S_H live at a time: a
+// reduced fraction p/q is read by a set when the set holds a multiple of q.
+__host__ __device__ constexpr bool in_hset(uint32_t M, int H) { return H >= 1 && H <= 32 && ((M >> (H - 1)) & 1u); }
+__host__ __device__ constexpr int hslot(uint32_t M, int H) {  // position of H among the set's members
+    int s = 0;
+    for (int h = 1; h < H; ++h) s += in_hset(M, h) ? 1 : 0;
+    return s;
+}
+__host__ __device__ constexpr int hset_size(uint32_t M) { return hslot(M, 33); }
+__host__ __device__ constexpr bool frac_in_hset(uint32_t M, int q) {
+    for (int m = 1; m * q <= 32; ++m)
+        if (in_hset(M, m * q)) return true;
+    return false;
+}
+__host__ __device__ constexpr uint32_t hset(std::initializer_list<int> hs) {
+    uint32_t m = 0;
+    for (int h : hs) m |= 1u << (h - 1);
+    return m;
 }
 
 }  // namespace hs

@@ -103,6 +103,32 @@ def test_calls_validate_before_device_work(hs_lib):
     hs_lib.hs_plan_destroy(pg)
 
 
+def test_binding_checks_input_type_against_plan(hs_lib):
+    """The C calls read the spectra as the plan's storage type through a bare pointer, so the binding
+    refuses a tensor of another type, non-contiguous spectra and non-int64 offsets before any call."""
+    torch = pytest.importorskip("torch")
+    p, _ = hs_lib.hs_plan_create(variants=hs_lib.FBIN, dtype=hs_lib.F32)
+    ph, _ = hs_lib.hs_plan_create(variants=hs_lib.FBIN, dtype=hs_lib.F16)
+    offs = torch.tensor([0, 64, 128], dtype=torch.int64)
+    out = hs_lib.Out()
+    ws = torch.empty(16, dtype=torch.uint8)
+    cases = [(p, torch.zeros(128, dtype=torch.float16), offs),
+             (ph, torch.zeros(128, dtype=torch.float32), offs),
+             (p, torch.zeros(128, dtype=torch.float64), offs),
+             (p, torch.zeros(256, dtype=torch.float32)[::2], offs),
+             (p, torch.zeros(128, dtype=torch.float32), offs.to(torch.int32))]
+    for plan, x, o in cases:
+        with pytest.raises(hs_lib.HSError) as e:
+            hs_lib.hs_sum_batched(plan, "fbin", x, o, out, ws)
+        assert e.value.status == hs_lib.ERR_INVALID
+        with pytest.raises(hs_lib.HSError):
+            hs_lib.hs_sum_batched_noalloc(plan, "fbin", x, o, out)
+    with pytest.raises(hs_lib.HSError):
+        hs_lib.hs_sum_1d(ph, "fbin", torch.zeros(64, dtype=torch.bfloat16), out, ws)
+    hs_lib.hs_plan_destroy(p)
+    hs_lib.hs_plan_destroy(ph)
+
+
 def test_library_noise_calibration_matches_oracle(hs_lib):
     for v in ("std", "max", "fbin", "greedy"):
         mu, isig = hs_lib.hs_noise_calibration(v, 32)
