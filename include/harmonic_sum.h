@@ -190,7 +190,9 @@ hs_status hs_sum_1d(const hs_plan* plan, hs_variant v, const void* d_x, int64_t 
  * d_offsets[s] * element size a multiple of 16).  Outputs are indexed by the same absolute
  * positions, so a batch may be any slice of a larger packed array.  One persistent launch walks a
  * work queue of (spectrum, tile) items; candidate spectrum ids are first_id + s.
- * hs_graph_create_batched captures this call in a CUDA graph for replay. */
+ * hs_graph_create_batched captures this call in a CUDA graph for replay.
+ * The library sees only the pointer: d_x must hold elements of the plan's dtype up to the last
+ * offset, or the kernels read past the caller's buffer (the Python binding checks this). */
 hs_status hs_sum_batched(const hs_plan* plan, hs_variant v, const void* d_x, const int64_t* d_offsets,
                          int n_spectra, uint32_t first_id, const hs_out* out, void* d_ws, size_t ws_bytes,
                          cudaStream_t stream);
