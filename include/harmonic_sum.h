@@ -350,6 +350,15 @@ int hs_plan_tile_bins(const hs_plan* plan, hs_variant v);
  * an earlier tuning run reported.  HS_ERR_INVALID otherwise. */
 hs_status hs_plan_set_tile_bins(hs_plan* plan, hs_variant v, int tile_bins);
 
+/* Batched calls run one persistent launch per variant, by default with as many 256-thread CTAs per SM
+ * as fit, so launches on other streams wait for its end.  A cap of 1..HS_MAX_CTAS_PER_SM CTAs per SM
+ * (0 restores the default) leaves room on every SM for a launch on another stream, e.g. Eq. 3 or 4
+ * beside Eq. 1; the results do not depend on it.  hs_plan_ctas_per_sm returns the cap (-1 for a bad
+ * argument); the setter returns HS_ERR_INVALID outside 0..HS_MAX_CTAS_PER_SM. */
+#define HS_MAX_CTAS_PER_SM 8
+int hs_plan_ctas_per_sm(const hs_plan* plan, hs_variant v);
+hs_status hs_plan_set_ctas_per_sm(hs_plan* plan, hs_variant v, int ctas_per_sm);
+
 /* Synchronise the stream and return the device status word of the workspace: HS_OK,
  * HS_WARN_CAND_OVERFLOW or HS_ERR_TIMEOUT.  Also reports a pending CUDA error as HS_ERR_CUDA. */
 hs_status hs_sync_status(const hs_plan* plan, const void* d_ws, cudaStream_t stream);

@@ -91,6 +91,8 @@ def _load():
         "hs_autotune_batched": ([_P, I, _P, _P, I, ctypes.POINTER(Out), _P, SZ, _P], I),
         "hs_plan_tile_bins": ([_P, I], I),
         "hs_plan_set_tile_bins": ([_P, I, I], I),
+        "hs_plan_ctas_per_sm": ([_P, I], I),
+        "hs_plan_set_ctas_per_sm": ([_P, I, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -333,6 +335,17 @@ def hs_plan_set_tile_bins(plan, variant, tile_bins):
     return _check(_lib.hs_plan_set_tile_bins(plan, _variant(variant), int(tile_bins)), "hs_plan_set_tile_bins")
 
 
+def hs_plan_ctas_per_sm(plan, variant) -> int:
+    return _lib.hs_plan_ctas_per_sm(plan, _variant(variant))
+
+
+def hs_plan_set_ctas_per_sm(plan, variant, ctas_per_sm):
+    """Cap a variant's persistent batched launch at ctas_per_sm CTAs per SM (0: as many as fit), so
+    that launches on other streams can run beside it."""
+    return _check(_lib.hs_plan_set_ctas_per_sm(plan, _variant(variant), int(ctas_per_sm)),
+                  "hs_plan_set_ctas_per_sm")
+
+
 def hs_sync_status(plan, ws, stream=None) -> int:
     return _check(_lib.hs_sync_status(plan, _ptr(ws), _stream(stream)), "hs_sync_status",
                   allow=(OK, WARN_CAND_OVERFLOW))
@@ -492,6 +505,7 @@ def _make_autograd_fn():
 # allocation-free batched entry point
 # ----------------------------------------------------------------------------------------------
 NOALLOC_MAX_SPECTRA = 16384
+MAX_CTAS_PER_SM = 8
 
 _lib.hs_sum_batched_noalloc.argtypes = [_P, ctypes.c_int, _P, _P, ctypes.c_int, ctypes.c_uint32, ctypes.POINTER(Out),
                                         _P]

@@ -934,7 +934,8 @@ static cudaError_t launch_zoned(const Tables& tab, const Work1d& w, const Out1d&
     }
     k_tile_scan<<<1, 1024, 0, s>>>(w.offsets, w.n_spectra, 0, w.max_bins, (int)sizeof(T), z, prefix, ctl);
     const int occ = zoned_occupancy<V, T, P2>();
-    k_hs1d_zoned<V, T, P2><<<(unsigned)(sm_count * occ), kBlock, 0, s>>>(tab, w, o, ctl, prefix);
+    const unsigned grid = persistent_grid(sm_count, occ, w.ctas_per_sm);
+    k_hs1d_zoned<V, T, P2><<<grid, kBlock, 0, s>>>(tab, w, o, ctl, prefix);
     return cudaGetLastError();
 }
 
@@ -964,8 +965,8 @@ static cudaError_t launch_eq1_pairs(const Tables& tab, const Work1d& w, const Ou
         return cudaGetLastError();
     }
     launch_tile_scan(w.offsets, w.n_spectra, tile, w.max_bins, (int)sizeof(T), prefix, ctl, s);
-    k_eq1_pairs_batched<T, P2><<<(unsigned)(sm_count * pair_occupancy<T, P2>()), kBlock, 0, s>>>(tab, w, o, ctl,
-                                                                                                prefix);
+    const unsigned grid = persistent_grid(sm_count, pair_occupancy<T, P2>(), w.ctas_per_sm);
+    k_eq1_pairs_batched<T, P2><<<grid, kBlock, 0, s>>>(tab, w, o, ctl, prefix);
     return cudaGetLastError();
 }
 
@@ -986,8 +987,8 @@ static cudaError_t launch_typed(const Tables& tab, const Work1d& w, const Out1d&
         return cudaGetLastError();
     }
     launch_tile_scan(w.offsets, w.n_spectra, tile, w.max_bins, (int)sizeof(T), prefix, ctl, s);
-    k_hs1d_batched<V, T, P2><<<(unsigned)(sm_count * occupancy<V, T, P2>()), kBlock, 0, s>>>(tab, w, o, ctl,
-                                                                                          prefix);
+    const unsigned pgrid = persistent_grid(sm_count, occupancy<V, T, P2>(), w.ctas_per_sm);
+    k_hs1d_batched<V, T, P2><<<pgrid, kBlock, 0, s>>>(tab, w, o, ctl, prefix);
     return cudaGetLastError();
 }
 

@@ -455,7 +455,8 @@ cudaError_t launch_typed(const Tables& tab, const Work1d& w, const Out1d& o, WsC
     if (e != cudaSuccess) return e;
     const uint32_t item_tiles = (uint32_t)std::max(1, w.opt * kBlock / kStB);
     launch_tile_scan(w.offsets, w.n_spectra, (int64_t)item_tiles * kStB, w.max_bins, (int)sizeof(T), prefix, ctl, s);
-    k_hs1d_eq1_staged<T><<<(unsigned)(sm_count * kStCtas), kStThreads, kStSmemBytes, s>>>(tab, w, o, ctl, prefix, item_tiles);
+    const unsigned grid = persistent_grid(sm_count, kStCtas, w.ctas_per_sm);
+    k_hs1d_eq1_staged<T><<<grid, kStThreads, kStSmemBytes, s>>>(tab, w, o, ctl, prefix, item_tiles);
     return cudaGetLastError();
 }
 

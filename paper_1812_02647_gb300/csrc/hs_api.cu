@@ -117,6 +117,7 @@ hs_status hs_plan_create(hs_plan** plan, const hs_plan_desc* d) {
     p->launch[1].opt = 4;  // Eq. 2
     p->launch[2].opt = 8;  // Eq. 3
     p->launch[3].opt = 8;  // Eq. 4
+    for (int k = 0; k < 4; ++k) p->launch[k].ctas_per_sm = 0;  // as many CTAs per SM as fit
     p->sm_count = 0;
     *plan = p;
     return HS_OK;
@@ -229,6 +230,7 @@ hs_status hs_sum_1d(const hs_plan* p, hs_variant v, const void* d_x, int64_t n_b
     w.hmax = p->d.hmax;
     w.threshold = p->d.threshold;
     w.opt = p->launch[vindex(v)].opt;
+    w.ctas_per_sm = p->launch[vindex(v)].ctas_per_sm;
     w.max_bins = p->d.max_bins;
     w.flags = p->d.flags;
     WsControl* ctl = reinterpret_cast<WsControl*>(d_ws);
@@ -256,6 +258,7 @@ hs_status hs_sum_batched(const hs_plan* p, hs_variant v, const void* d_x, const 
     w.hmax = p->d.hmax;
     w.threshold = p->d.threshold;
     w.opt = p->launch[vindex(v)].opt;
+    w.ctas_per_sm = p->launch[vindex(v)].ctas_per_sm;
     w.max_bins = p->d.max_bins;
     w.flags = p->d.flags;
     WsControl* ctl = reinterpret_cast<WsControl*>(d_ws);

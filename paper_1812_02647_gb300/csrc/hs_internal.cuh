@@ -58,12 +58,21 @@ struct Work1d {
     float threshold;
     int opt;        // outputs per thread; a tile is kBlock * opt output bins
     int64_t max_bins;
-    int flags;      // plan flags (HS_FLAG_*)
+    int flags;        // plan flags (HS_FLAG_*)
+    int ctas_per_sm;  // persistent batched launches: CTAs per SM (0: as many as fit)
 };
 
 struct Launch {
-    int opt;  // outputs per thread
+    int opt;          // outputs per thread
+    int ctas_per_sm;  // 0: as many as fit
 };
+
+// Grid of a persistent launch: occ CTAs fit on an SM; a plan may ask for fewer, so that launches on
+// other streams find room beside it.
+inline unsigned persistent_grid(int sm_count, int occ, int ctas_per_sm) {
+    const int k = ctas_per_sm > 0 && ctas_per_sm < occ ? ctas_per_sm : occ;
+    return (unsigned)(sm_count * (k > 0 ? k : 1));
+}
 
 // Values worth computing once per device (occupancies, function attributes): slot d of an array of
 // kMaxDevices belongs to device ordinal d.  A device ordinal beyond the table shares slot 0.

@@ -79,6 +79,7 @@ extern "C" hs_status hs_sum_batched_noalloc(const hs_plan* p, hs_variant v, cons
     w.hmax = p->d.hmax;
     w.threshold = p->d.threshold;
     w.opt = p->launch[vindex(v)].opt;
+    w.ctas_per_sm = p->launch[vindex(v)].ctas_per_sm;
     w.max_bins = p->d.max_bins;
     w.flags = p->d.flags;
     Out1d o;

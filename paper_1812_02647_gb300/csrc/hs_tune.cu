@@ -171,6 +171,17 @@ extern "C" int hs_plan_tile_bins(const hs_plan* p, hs_variant v) {
     return kBlock * p->launch[vindex(v)].opt;
 }
 
+extern "C" int hs_plan_ctas_per_sm(const hs_plan* p, hs_variant v) {
+    if (!p || vindex(v) < 0) return -1;
+    return p->launch[vindex(v)].ctas_per_sm;
+}
+
+extern "C" hs_status hs_plan_set_ctas_per_sm(hs_plan* p, hs_variant v, int ctas_per_sm) {
+    if (!p || vindex(v) < 0 || ctas_per_sm < 0 || ctas_per_sm > HS_MAX_CTAS_PER_SM) return HS_ERR_INVALID;
+    p->launch[vindex(v)].ctas_per_sm = ctas_per_sm;
+    return HS_OK;
+}
+
 extern "C" hs_status hs_plan_set_tile_bins(hs_plan* p, hs_variant v, int tile_bins) {
     if (!p || vindex(v) < 0 || tile_bins < kBlock || tile_bins > 64 * kBlock || tile_bins % kBlock != 0)
         return HS_ERR_INVALID;

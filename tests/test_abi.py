@@ -42,6 +42,7 @@ def test_binding_constants_match_the_header(hs_lib):
     """The Python binding restates some header constants; they must not drift apart."""
     d = header_defines()
     assert int(d["HS_NOALLOC_MAX_SPECTRA"]) == hs_lib.NOALLOC_MAX_SPECTRA
+    assert int(d["HS_MAX_CTAS_PER_SM"]) == hs_lib.MAX_CTAS_PER_SM
     assert int(d["HS_HMAX_1D"]) == hs_lib.HMAX_1D and int(d["HS_HMAX_2D"]) == hs_lib.HMAX_2D
     for name in ("OUT_ALL_H", "STAGED_SPANS", "MAX_WINDOW0", "POW2_STAGES", "GREEDY_FIXED1", "CHECK_TIMEOUT"):
         assert int(d["HS_FLAG_" + name]) == getattr(hs_lib, "FLAG_" + name), name
@@ -127,6 +128,21 @@ def test_binding_checks_input_type_against_plan(hs_lib):
         hs_lib.hs_sum_1d(ph, "fbin", torch.zeros(64, dtype=torch.bfloat16), out, ws)
     hs_lib.hs_plan_destroy(p)
     hs_lib.hs_plan_destroy(ph)
+
+
+def test_ctas_per_sm_cap_arguments(hs_lib):
+    p, _ = hs_lib.hs_plan_create(variants=0xF)
+    for v in ("std", "max", "fbin", "greedy"):
+        assert hs_lib.hs_plan_ctas_per_sm(p, v) == 0  # default: as many as fit
+    hs_lib.hs_plan_set_ctas_per_sm(p, "fbin", hs_lib.MAX_CTAS_PER_SM)
+    assert hs_lib.hs_plan_ctas_per_sm(p, "fbin") == hs_lib.MAX_CTAS_PER_SM
+    for bad in (-1, hs_lib.MAX_CTAS_PER_SM + 1):
+        with pytest.raises(hs_lib.HSError) as e:
+            hs_lib.hs_plan_set_ctas_per_sm(p, "std", bad)
+        assert e.value.status == hs_lib.ERR_INVALID
+    assert hs_lib._lib.hs_plan_set_ctas_per_sm(p, 3, 1) == hs_lib.ERR_INVALID  # not a single variant
+    assert hs_lib._lib.hs_plan_ctas_per_sm(None, 1) == -1
+    hs_lib.hs_plan_destroy(p)
 
 
 def test_library_noise_calibration_matches_oracle(hs_lib):

@@ -516,6 +516,38 @@ def test_autotune_batched_keeps_results(hs_lib, torch):
         np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
 
 
+@pytest.mark.parametrize("caps", [(1, 1, 1, 1), (3, 1, 2, 1)])
+def test_ctas_per_sm_cap_and_concurrent_streams_keep_results(hs_lib, torch, caps):
+    """Persistent launches capped at k CTAs per SM, Eq. 1 on one stream and Eq. 2-4 on another at the
+    same time (the caps leave room on every SM for both), equal the oracle bit for bit."""
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(12, lengths=(1 << 16, 1 << 18))
+    x = hs_synth.batch(seed, offsets, pulsars)
+    xd, od = torch.from_numpy(x).cuda(), torch.from_numpy(offsets).cuda()
+    hs = hs_lib.HarmonicSum(variants=0xF, threshold=THR, cand_capacity=x.size, max_spectra=12)
+    ws2 = torch.empty_like(hs.ws)
+    hs_lib.hs_workspace_init(hs.plan, ws2)
+    for v, k in zip(VARIANTS, caps):
+        hs_lib.hs_plan_set_ctas_per_sm(hs.plan, v, k)
+        assert hs_lib.hs_plan_ctas_per_sm(hs.plan, v) == k
+    outs = {v: hs.new_outputs(x.size, v, "cuda") for v in VARIANTS}
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        hs_lib.hs_sum_batched(hs.plan, "std", xd, od, hs.out_struct(outs["std"]), hs.ws, stream=s1)
+    with torch.cuda.stream(s2):
+        for v in ("max", "fbin", "greedy"):
+            hs_lib.hs_sum_batched(hs.plan, v, xd, od, hs.out_struct(outs[v]), ws2, stream=s2)
+    torch.cuda.synchronize()
+    assert hs_lib.hs_sync_status(hs.plan, hs.ws) == hs_lib.OK
+    assert hs_lib.hs_sync_status(hs.plan, ws2) == hs_lib.OK
+    for v in VARIANTS:
+        r = oracle.hs_batched(v, x, offsets, nthreads=8)
+        np.testing.assert_array_equal(outs[v]["best_snr"].cpu().numpy(), r["best_snr"])
+        np.testing.assert_array_equal(outs[v]["best_h"].cpu().numpy(), r["best_h"])
+    hs_lib.hs_plan_set_ctas_per_sm(hs.plan, "std", 0)
+    assert hs_lib.hs_plan_ctas_per_sm(hs.plan, "std") == 0
+
+
 def test_autotune_keeps_results(hs_lib, torch):
     N = 1 << 20
     x = hs_synth.spectrum(13, 0, N)
