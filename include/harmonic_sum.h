@@ -170,7 +170,11 @@ hs_status hs_noise_calibration_flags(hs_variant v, int hmax, int flags, float* m
 /* Bytes of device workspace a call needs for up to n_spectra spectra (1 for hs_sum_1d / 2-D).
  * The workspace holds the status word, the work queue and tile prefix sums; it must be 256-byte
  * aligned, must not be shared by calls that may overlap on the GPU, and is zeroed by
- * hs_workspace_init. */
+ * hs_workspace_init.  A plan with FP16/BF16 storage, Eq. 1 and hmax 32 (without
+ * HS_FLAG_STAGED_SPANS) also reserves min(n_spectra, 64) * max_bins * 4 bytes: batched Eq. 1 widens
+ * up to 64 consecutive spectra at a time into FP32 there and sums them with the FP32 kernel (exact:
+ * the same values and operations), which requires non-decreasing offsets (a spectrum outside its
+ * group's range is skipped and reported as HS_ERR_INVALID by hs_sync_status). */
 hs_status hs_plan_workspace_size(const hs_plan* plan, int n_spectra, size_t* bytes);
 
 /* Zero the workspace status word on the stream (call once after allocating the workspace and

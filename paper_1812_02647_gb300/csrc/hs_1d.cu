@@ -809,7 +809,9 @@ __global__ void __launch_bounds__(kBlock, Eq1Passes<T>::min_blocks) k_eq1_pairs_
     eq1_pair_tile<T, P2>((const T*)w.x, N, t0, min(N, t0 + tile), tb, w, o, 0, w.first_id, &ctl->status);
 }
 
-template <typename T, bool P2>
+// REBASE: w.x holds elements offsets[0] .. of the batch rather than the batch itself (a group of
+// spectra widened into FP32); outputs keep the batch's absolute positions.
+template <typename T, bool P2, bool REBASE = false>
 __global__ void __launch_bounds__(kBlock, Eq1Passes<T>::min_blocks) k_eq1_pairs_batched(const __grid_constant__ Tables tb,
                                                                                 const Work1d w, const Out1d o,
                                                                                 WsControl* ctl, const int64_t* prefix) {
@@ -832,8 +834,19 @@ __global__ void __launch_bounds__(kBlock, Eq1Passes<T>::min_blocks) k_eq1_pairs_
         const int64_t off = w.offsets[s];
         const uint32_t N = (uint32_t)(w.offsets[s + 1] - off);
         const uint32_t t0 = (uint32_t)(item - (unsigned long long)prefix[s]) * tile;
-        eq1_pair_tile<T, P2>((const T*)w.x + off, N, t0, min(N, t0 + tile), tb, w, o, (size_t)off,
-                             w.first_id + (uint32_t)s, &ctl->status);
+        int64_t in_off = off;
+        bool inside = true;
+        if constexpr (REBASE) {
+            // the spectrum must lie in the widened range, and the range must have fit (offsets that
+            // are not monotone can give a spectrum of valid length outside it)
+            const int64_t base = w.offsets[0], end = w.offsets[w.n_spectra];
+            inside = off >= base && off + (int64_t)N <= end && end - base <= (int64_t)w.n_spectra * w.max_bins;
+            in_off = off - base;
+            if (!inside && threadIdx.x == 0) atomicOr(&ctl->status, kStatusBadInput);
+        }
+        if (inside)
+            eq1_pair_tile<T, P2>((const T*)w.x + in_off, N, t0, min(N, t0 + tile), tb, w, o, (size_t)off,
+                                 w.first_id + (uint32_t)s, &ctl->status);
         __syncthreads();  // every thread has read s_item / s_spec
         if (threadIdx.x == 0) {
             s_item = next;
@@ -841,6 +854,41 @@ __global__ void __launch_bounds__(kBlock, Eq1Passes<T>::min_blocks) k_eq1_pairs_
         }
         __syncthreads();
     }
+}
+
+// Elements offsets[0] .. offsets[n] of a 16-bit batch widened to FP32 (exactly) at out[0 ..), eight
+// per thread and step when the range starts 16-byte aligned.  A range that is reversed or longer than
+// cap elements is left alone (the tile scan reports the bad layout; its spectra get no work).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_widen(const T* x, const int64_t* offsets, int n, int64_t cap,
+                                                  float* out) {
+    const int64_t base = offsets[0], end = offsets[n];
+    if (base < 0 || end < base || end - base > cap) return;
+    const int64_t len = end - base;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const T* src = x + base;
+    int64_t done = 0;
+    if ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
+        const int64_t n8 = len / 8;
+        for (int64_t i = t; i < n8; i += stride) {
+            const uint4 raw = __ldg(reinterpret_cast<const uint4*>(src) + i);
+            const T* e = reinterpret_cast<const T*>(&raw);
+            float4 lo, hi;
+            lo.x = widen<T>(e[0]);
+            lo.y = widen<T>(e[1]);
+            lo.z = widen<T>(e[2]);
+            lo.w = widen<T>(e[3]);
+            hi.x = widen<T>(e[4]);
+            hi.y = widen<T>(e[5]);
+            hi.z = widen<T>(e[6]);
+            hi.w = widen<T>(e[7]);
+            reinterpret_cast<float4*>(out)[2 * i] = lo;
+            reinterpret_cast<float4*>(out)[2 * i + 1] = hi;
+        }
+        done = n8 * 8;
+    }
+    for (int64_t i = done + t; i < len; i += stride) out[i] = widen<T>(src[i]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -900,25 +948,54 @@ static cudaError_t launch_zoned(const Tables& tab, const Work1d& w, const Out1d&
     return cudaGetLastError();
 }
 
-template <typename T, bool P2>
+template <typename T, bool P2, bool REBASE>
 static int& pair_occupancy_slot() {
     static int occ[kMaxDevices] = {};  // resident CTAs per SM of the persistent Eq. 1 pair kernel, per device
     return occ[device_slot()];
 }
 
-template <typename T, bool P2>
+template <typename T, bool P2, bool REBASE = false>
 static int pair_occupancy() {
-    int& oc = pair_occupancy_slot<T, P2>();
+    int& oc = pair_occupancy_slot<T, P2, REBASE>();
     if (oc == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_eq1_pairs_batched<T, P2>, kBlock, 0);
+        cudaError_t e =
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&oc, k_eq1_pairs_batched<T, P2, REBASE>, kBlock, 0);
         if (e != cudaSuccess || oc < 1) oc = 1;
     }
     return oc;
 }
 
+// A 16-bit batch with a staging region: groups of up to kStageSpectra consecutive spectra (one
+// contiguous range of the batch) are widened into the region and summed by the FP32 kernel, which
+// reads them rebased and writes the batch's output positions.  Bit-identical to the 16-bit kernel
+// (widening is exact and the sums are the same FP32 operations in the same order).
+template <typename T, bool P2>
+static cudaError_t launch_eq1_widened(const Tables& tab, const Work1d& w, const Out1d& o, WsControl* ctl,
+                                      int64_t* prefix, int sm_count, cudaStream_t s) {
+    const int64_t tile = (int64_t)kBlock * w.opt;
+    const unsigned grid = persistent_grid(sm_count, pair_occupancy<float, P2, true>(), w.ctas_per_sm);
+    Work1d g = w;
+    g.x = w.stage;
+    for (int g0 = 0; g0 < w.n_spectra; g0 += kStageSpectra) {
+        const int ng = std::min(kStageSpectra, w.n_spectra - g0);
+        k_widen<T><<<(unsigned)(sm_count * 8), kBlock, 0, s>>>((const T*)w.x, w.offsets + g0, ng,
+                                                              (int64_t)ng * w.max_bins, w.stage);
+        g.offsets = w.offsets + g0;
+        g.n_spectra = ng;
+        g.first_id = w.first_id + (uint32_t)g0;
+        // the layout checks use the storage type's alignment, so a spectrum the 16-bit kernel would
+        // refuse is refused here too
+        launch_tile_scan(g.offsets, ng, tile, w.max_bins, (int)sizeof(T), prefix, ctl, s);
+        k_eq1_pairs_batched<float, P2, true><<<grid, kBlock, 0, s>>>(tab, g, o, ctl, prefix);
+    }
+    return cudaGetLastError();
+}
+
 template <typename T, bool P2>
 static cudaError_t launch_eq1_pairs(const Tables& tab, const Work1d& w, const Out1d& o, WsControl* ctl,
                                     int64_t* prefix, int sm_count, cudaStream_t s) {
+    if constexpr (sizeof(T) == 2)
+        if (w.offsets != nullptr && w.stage != nullptr) return launch_eq1_widened<T, P2>(tab, w, o, ctl, prefix, sm_count, s);
     const int64_t tile = (int64_t)kBlock * w.opt;
     if (w.offsets == nullptr) {
         if (w.n_bins == 0) return cudaSuccess;

@@ -187,9 +187,18 @@ hs_status hs_noise_calibration_flags(hs_variant v, int hmax, int flags, float* m
     return HS_OK;
 }
 
+// Eq. 1 of a 16-bit plan runs batches through an FP32 copy of up to kStageSpectra spectra at a time
+// (the FP32 pair kernel is faster than any 16-bit form of it measured), held in the workspace.
+static bool stages_eq1(const hs_plan* p) {
+    return p->d.dtype != HS_F32 && (p->d.variants & HS_STD) && p->d.hmax == kHmax &&
+           !(p->d.flags & HS_FLAG_STAGED_SPANS);
+}
+
 hs_status hs_plan_workspace_size(const hs_plan* p, int n_spectra, size_t* bytes) {
     if (!p || !bytes || n_spectra < 0) return HS_ERR_INVALID;
-    size_t a = ws_bytes_for(n_spectra < 1 ? 1 : n_spectra);
+    const int ns = n_spectra < 1 ? 1 : n_spectra;
+    size_t a = ws_bytes_for(ns);
+    if (stages_eq1(p)) a = stage_offset(ns) + stage_bytes(ns, p->d.max_bins);
     size_t b = sort_scratch_bytes(p->d.cand_capacity);
     *bytes = (a > b ? a : b + 0);
     *bytes = (*bytes + 255) & ~(size_t)255;
@@ -261,6 +270,9 @@ hs_status hs_sum_batched(const hs_plan* p, hs_variant v, const void* d_x, const 
     w.ctas_per_sm = p->launch[vindex(v)].ctas_per_sm;
     w.max_bins = p->d.max_bins;
     w.flags = p->d.flags;
+    w.stage = (v == HS_STD && stages_eq1(p))
+                  ? reinterpret_cast<float*>(reinterpret_cast<char*>(d_ws) + stage_offset(n_spectra))
+                  : nullptr;
     WsControl* ctl = reinterpret_cast<WsControl*>(d_ws);
     int64_t* prefix = reinterpret_cast<int64_t*>(reinterpret_cast<char*>(d_ws) + kWsControlBytes);
     return check_cuda(launch_1d(v, p->d.dtype, p->tab[vindex(v)], w, make_out(p, v, out), ctl, prefix,

@@ -30,6 +30,17 @@ inline size_t ws_bytes_for(int n_spectra) {
     return kWsControlBytes + sizeof(int64_t) * (size_t)(n_spectra + 2);
 }
 
+// Eq. 1 over 16-bit storage in a batch widens up to kStageSpectra spectra at a time into FP32 in the
+// workspace, after the prefix sums, and runs the FP32 kernel on them.
+constexpr int kStageSpectra = 64;
+inline size_t stage_offset(int n_spectra) {
+    return (ws_bytes_for(n_spectra) + 255) & ~(size_t)255;
+}
+inline size_t stage_bytes(int n_spectra, int64_t max_bins) {
+    const int g = n_spectra < kStageSpectra ? n_spectra : kStageSpectra;
+    return (size_t)(g < 1 ? 1 : g) * (size_t)max_bins * sizeof(float);
+}
+
 // Scale and calibration of one variant: snr_H = (S_H * c[H] - mu[H]) * isig[H].
 struct Tables {
     float c[kHmax + 1];
@@ -60,6 +71,7 @@ struct Work1d {
     int64_t max_bins;
     int flags;        // plan flags (HS_FLAG_*)
     int ctas_per_sm;  // persistent batched launches: CTAs per SM (0: as many as fit)
+    float* stage;     // FP32 staging of 16-bit spectra for Eq. 1 (batched calls), or nullptr
 };
 
 struct Launch {

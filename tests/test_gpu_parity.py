@@ -206,6 +206,51 @@ def test_batched_staged_spans_bit_exact(hs_lib, torch, dtype):
         _check_candidates(hs_lib, o, r["best_snr"], r["best_h"], offsets, first_id=7)
 
 
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_eq1_16bit_batch_through_fp32_groups(hs_lib, torch, dtype):
+    """Eq. 1 of a 16-bit batch runs groups of up to 64 spectra through an FP32 copy in the workspace:
+    141 spectra (three groups, the last short), empty and ragged spectra, a batch slice with absolute
+    offsets, equal to the FP32 oracle on the widened values."""
+    rng = np.random.default_rng(5)
+    lens = [int(rng.integers(0, 20000)) for _ in range(140)] + [12345]
+    lens[3] = lens[40] = 0
+    lens = [(l + 7) // 8 * 8 for l in lens[:-1]] + [lens[-1]]  # 16-byte aligned starts
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    offsets += 64  # the batch starts 64 elements into the buffer
+    x32 = hs_synth.batch(41, np.concatenate([[0], offsets]))
+    xd, xw = _widen(torch, x32, dtype)
+    code = {"f16": 1, "bf16": 2}[dtype]
+    hs, mu, isig = _make(hs_lib, "std", True, dtype=code, max_bins=1 << 16, flags=0, max_spectra=len(lens),
+                         cap=1 << 18)
+    o = hs.new_outputs(xd.numel(), "std", "cuda")
+    o["best_snr"].fill_(-123.0)
+    hs_lib.hs_sum_batched(hs.plan, "std", xd, torch.from_numpy(offsets).cuda(), hs.out_struct(o), hs.ws, 5)
+    assert hs.sync_status() == hs_lib.OK
+    r = oracle.hs_batched("std", xw, offsets, mu=mu, isig=isig, nthreads=8)
+    got = o["best_snr"].cpu().numpy()  # the oracle's arrays start at the batch's first offset
+    np.testing.assert_array_equal(got[64:], r["best_snr"])
+    np.testing.assert_array_equal(o["best_h"].cpu().numpy()[64:], r["best_h"])
+    assert np.all(got[:64] == -123.0)  # outside the batch: untouched
+    _check_candidates(hs_lib, o, r["best_snr"], r["best_h"], offsets - 64, first_id=5)
+
+
+def test_eq1_16bit_groups_refuse_spectra_outside_the_widened_range(hs_lib, torch):
+    """Offsets that are not monotone: a spectrum of valid length that lies outside its group's
+    widened range is skipped and reported (HS_ERR_INVALID from the status word), never read."""
+    x32 = hs_synth.batch(42, np.array([0, 4096], np.int64))
+    xd, _ = _widen(torch, x32, "f16")
+    hs, _, _ = _make(hs_lib, "std", True, dtype=1, max_bins=4096, flags=0, max_spectra=3)
+    offsets = np.array([1024, 2048, 0, 512], np.int64)  # [1024, 2048) valid, then negative, then [0, 512)
+    o = hs.new_outputs(xd.numel(), "std", "cuda")
+    o["best_snr"].fill_(-123.0)
+    hs_lib.hs_sum_batched(hs.plan, "std", xd, torch.from_numpy(offsets).cuda(), hs.out_struct(o), hs.ws)
+    with pytest.raises(hs_lib.HSError) as e:
+        hs.sync_status()
+    assert e.value.status == hs_lib.ERR_INVALID
+    assert np.all(o["best_snr"].cpu().numpy() == -123.0)
+
+
 def test_staged_spans_slice_and_graph(hs_lib, torch):
     """The staged path on a batch slice with absolute offsets, captured in a graph and replayed."""
     seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(12, lengths=(1 << 15, 1 << 16, 1 << 17))

@@ -47,6 +47,36 @@ def test_noalloc_matches_workspace_entry_point(hs_lib):
             np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_noalloc_16bit_eq1_matches_the_fp32_groups(hs_lib, dtype):
+    """For 16-bit storage the workspace entry point runs Eq. 1 through FP32 copies of 64-spectrum
+    groups while the allocation-free one runs the 16-bit kernel directly: the two agree bit for bit."""
+    import torch
+
+    rng = np.random.default_rng(11)
+    lens = [int(rng.integers(1, 3000)) * 8 for _ in range(90)]
+    offsets = np.zeros(len(lens) + 1, np.int64)
+    np.cumsum(lens, out=offsets[1:])
+    tdt = {"f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    xd = torch.from_numpy(hs_synth.batch(304, offsets)).to(tdt).cuda()
+    od = torch.from_numpy(offsets).cuda()
+    hs = hs_lib.HarmonicSum(variants=hs_lib.STD, dtype={"f16": hs_lib.F16, "bf16": hs_lib.BF16}[dtype],
+                            max_bins=1 << 16, threshold=6.0, cand_capacity=1 << 16, max_spectra=len(lens))
+    mu, isig = hs_lib.hs_noise_calibration("std", 32)
+    hs.set_calibration("std", mu, isig)
+    ref = hs.sum_batched("std", xd, od, first_id=2)
+    torch.cuda.synchronize()
+    assert hs.sync_status() == hs_lib.OK
+    o = hs.new_outputs(xd.numel(), "std", "cuda")
+    hs_lib.hs_sum_batched_noalloc(hs.plan, "std", xd, od, hs.out_struct(o), first_id=2)
+    torch.cuda.synchronize()
+    assert torch.equal(o["best_snr"], ref["best_snr"])
+    assert torch.equal(o["best_h"], ref["best_h"])
+    a = np.sort(hs_lib.read_candidates(o), order=["spectrum", "bin"])
+    b = np.sort(hs_lib.read_candidates(ref), order=["spectrum", "bin"])
+    np.testing.assert_array_equal(a, b)
+
+
 def test_noalloc_staged_spans_matches_workspace_entry_point(hs_lib):
     """Eq. 1 through the staged-span kernel (HS_FLAG_STAGED_SPANS), the one path with bounded
     device waits and its own tile size over the same prefix array."""
