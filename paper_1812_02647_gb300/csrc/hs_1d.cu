@@ -862,6 +862,7 @@ __global__ void __launch_bounds__(kBlock, Eq1Passes<T>::min_blocks) k_eq1_pairs_
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_widen(const T* x, const int64_t* offsets, int n, int64_t cap,
                                                   float* out) {
+    static_assert(sizeof(T) == 2, "16-bit storage: eight elements per 16-byte load");
     const int64_t base = offsets[0], end = offsets[n];
     if (base < 0 || end < base || end - base > cap) return;
     const int64_t len = end - base;
