@@ -472,8 +472,12 @@ def _sec_adjoint(torch, hs, stream, tiles, reps, fdas_bins):
             hs.hs_backward(h.plan, v, x, od, g, o["best_h"], o.get("path"), gx, stream)
 
         b = _time_ms(torch, stream, bwd, reps)
+        # the backward scatters one FP32 atomic add per term of the chosen S_H*: H* per bin
+        updates = int(o["best_h"].to(torch.int64).sum().item())
         adj[v] = {"forward_ms": fwd, "backward_ms": b, "backward_over_forward": b / fwd,
-                  "value_fwd_bwd": total * HMAX / ((fwd + b) / 1e3)}
+                  "value_fwd_bwd": total * HMAX / ((fwd + b) / 1e3),
+                  "atomic_updates_per_bin": updates / total,
+                  "atomic_updates_per_s": updates / (b / 1e3)}
         del h, o, g, gx
     return {"workload": "256 spectra x 2^20 bins FP32, loss = sum softplus(snr - 5)", **adj}
 
