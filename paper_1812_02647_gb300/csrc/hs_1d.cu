@@ -111,7 +111,8 @@ __device__ __forceinline__ void pair_pass(const T* x, uint32_t n, const Tables& 
 }
 // Passes per storage type: FP32 runs the three passes at four CTAs per SM; FP16/BF16 spend two more
 // instructions per fraction on widening and measured faster as one pass over all 32 sums at two CTAs
-// per SM (369 against 501 ms on 4096 x 2^20 bins).
+// per SM (369 against 501 ms on 4096 x 2^20 bins).  Batched calls with a workspace do not use the
+// 16-bit kernel at all: they widen groups of spectra and run the FP32 one (launch_eq1_widened).
 template <typename T>
 struct Eq1Passes {
     static constexpr bool split = std::is_same<T, float>::value;
