@@ -435,10 +435,12 @@ struct MinBlocks {
 
 // the zoned kernels carry one copy of the bin loop per unrolled count.  Eq. 3 runs at full occupancy
 // (32 registers, a few spilled): its loads are independent and latency-bound, and eight CTAs per SM
-// measured 3-7% faster than six.
-template <int V>
+// measured 3-7% faster than six.  Eq. 2 at five CTAs per SM (48 registers) measured 8% faster than
+// at four for FP32, whose six-CTA build spills heavily; 16-bit storage gains 3% more at six.  Eq. 4
+// is fastest at five (six and eight measured slower).
+template <int V, typename T>
 struct ZonedMinBlocks {
-    static constexpr int value = V == HS_MAX ? 4 : (V == HS_FBIN ? 8 : 5);
+    static constexpr int value = V == HS_MAX ? (sizeof(T) == 2 ? 6 : 5) : (V == HS_FBIN ? 8 : 5);
 };
 
 // Eq. 2 indexes the calibration tables by a runtime H, which is cheaper from shared memory than
@@ -608,7 +610,7 @@ __device__ __forceinline__ void zone_dispatch(const T* x, uint32_t N, uint32_t l
 
 // One spectrum: CTA b runs work item b.
 template <int V, typename T, bool P2>
-__global__ void __launch_bounds__(kBlock, ZonedMinBlocks<V>::value) k_hs1d_zoned_single(const __grid_constant__ Tables tb_param,
+__global__ void __launch_bounds__(kBlock, ZonedMinBlocks<V, T>::value) k_hs1d_zoned_single(const __grid_constant__ Tables tb_param,
                                                                                   const Work1d w, const Out1d o,
                                                                                   WsControl* ctl) {
     __shared__ Tables s_tb;
@@ -669,7 +671,7 @@ __device__ __forceinline__ void zone_resolve(const ZoneSpec& z, const Work1d& w,
 // resolves the next item at the start of the current one (into the other of two slots), so the
 // lookup's memory latency overlaps the other warps' work on the current item.
 template <int V, typename T, bool P2>
-__global__ void __launch_bounds__(kBlock, ZonedMinBlocks<V>::value) k_hs1d_zoned(const __grid_constant__ Tables tb_param,
+__global__ void __launch_bounds__(kBlock, ZonedMinBlocks<V, T>::value) k_hs1d_zoned(const __grid_constant__ Tables tb_param,
                                                                                 const Work1d w, const Out1d o,
                                                                                 WsControl* ctl, const int64_t* prefix) {
     __shared__ Tables s_tb;
