@@ -816,7 +816,7 @@ def main():
     if dom == "std":
         # Eq. 1 performs 528 ordered FP32 adds per bin (sum_{H<=32} H); its HBM bytes are negligible
         tf = 528.0 * total / (avg[dom] / 1e3) / 1e12
-        kname = "hs::k_hs1d_eq1_staged" if args.staged_spans else "hs::k_eq1_pairs_batched<float, false>"
+        kname = "hs::k_hs1d_eq1_staged" if args.staged_spans else "hs::k_eq1_pairs_batched<float, false, false>"
         roof = {"bound": "alu", "kernel": kname, "achieved": tf, "peak": alu_peak,
                 "peak_source": "derived: SMs x 128 FP32 lanes x max SM clock", "unit": "TFLOP/s",
                 "frac": tf / alu_peak, "traffic": traffic, "algorithmic_flops_per_launch": 528.0 * total}
