@@ -71,20 +71,6 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def measure_l2_copy_gbs(torch, stream, mib=24, reps=200):
-    """L2-resident copy rate through the SMs (read + write bytes / time): an elementwise kernel that
-    reads one buffer of `mib` MiB and writes another, both far below the L2 capacity; the L2
-    counterpart of the HBM copy figure (a device-to-device memcpy would not run on the SMs)."""
-    n = mib * (1 << 20) // 4
-    a = torch.ones(n, device="cuda")
-    b = torch.empty_like(a)
-    for _ in range(10):
-        torch.mul(a, 2.0, out=b)
-    ms = _time_ms(torch, stream, lambda: torch.mul(a, 2.0, out=b), reps)
-    del a, b
-    return 2 * n * 4 / (ms / 1e3) / 1e9
-
-
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
 
@@ -796,8 +782,6 @@ def main():
             prof = tj.get("kernels", {})
     except Exception:
         pass
-    with torch.cuda.stream(stream):
-        l2_peak = measure_l2_copy_gbs(torch, stream)
     per_roof = {}
     for v in variants:
         gbs = compulsory_bytes(v) / (avg[v] / 1e3) / 1e9
@@ -805,10 +789,14 @@ def main():
                        "kernel": prof.get(v, {}).get("kernel")}
         if v in prof:
             l2b = prof[v]["l2_read_bytes_per_bin"] * total
+            # L2-to-L1 bytes of this launch (ncu bytes per bin x bins) over its time, and how busy ncu
+            # found the L2 (lts__throughput, % of its peak) on a capture of the same sources
+            pct = (prof[v].get("ncu_pct") or {}).get("l2_throughput_of_peak")
             per_roof[v]["l2"] = {"bytes_per_launch": l2b, "bytes_per_bin": prof[v]["l2_read_bytes_per_bin"],
-                                 "achieved": l2b / (avg[v] / 1e3) / 1e9, "peak": l2_peak, "unit": "GB/s",
-                                 "frac": l2b / (avg[v] / 1e3) / 1e9 / l2_peak,
-                                 "peak_source": "measured in this run: L2-resident 24 MiB elementwise copy"}
+                                 "achieved": l2b / (avg[v] / 1e3) / 1e9, "unit": "GB/s",
+                                 "frac": None if pct is None else pct / 100.0,
+                                 "peak_source": "ncu lts__throughput.avg.pct_of_peak_sustained_elapsed of the same "
+                                                "kernel (32-spectrum capture of the same sources)"}
             per_roof[v]["traffic"] = prof[v]["dram_bytes_per_bin"] * total
             per_roof[v]["ncu_pct_of_peak"] = prof[v].get("ncu_pct")
     traffic = prof["std"]["dram_bytes_per_bin"] * total if "std" in prof else None
