@@ -638,6 +638,34 @@ def test_host_batch_streamed_matches_device_batch(hs_lib, torch, n_chunks):
         np.testing.assert_array_equal(a, b)
 
 
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+def test_host_batch_streamed_16bit_eq1(hs_lib, torch, dtype):
+    """A 16-bit host batch streamed in pieces: Eq. 1 of every piece runs through the FP32 groups of
+    the workspace (sized for the whole batch, used per piece) and equals the oracle on the widened
+    values."""
+    seed, offsets, pulsars = hs_synth.batch_dm_trials_layout(70, lengths=(1 << 12, 1 << 13, 1 << 14))
+    total = int(offsets[-1])
+    x32 = hs_synth.batch(seed, offsets, pulsars)
+    tdt = {"f16": torch.float16, "bf16": torch.bfloat16}[dtype]
+    xs = torch.from_numpy(x32).to(tdt)
+    xh = torch.empty(total, dtype=tdt, pin_memory=True)
+    xh.copy_(xs)
+    xw = xs.float().numpy()
+    hs, mu, isig = _make(hs_lib, "std", True, dtype={"f16": 1, "bf16": 2}[dtype], max_bins=1 << 14, flags=0,
+                         max_spectra=70)
+    xd = torch.empty(total, dtype=tdt, device="cuda")
+    od = torch.empty(71, dtype=torch.int64, device="cuda")
+    r = oracle.hs_batched("std", xw, offsets, mu=mu, isig=isig, nthreads=8)
+    for n_chunks in (1, 3):
+        o = hs.new_outputs(total, "std", "cuda")
+        hs_lib.hs_sum_batched_host(hs.plan, hs_lib.STD, xh, offsets, xd, od, [hs.out_struct(o)], hs.ws,
+                                   n_chunks=n_chunks)
+        torch.cuda.synchronize()
+        assert hs.sync_status() == hs_lib.OK
+        np.testing.assert_array_equal(o["best_snr"].cpu().numpy(), r["best_snr"])
+        np.testing.assert_array_equal(o["best_h"].cpu().numpy(), r["best_h"])
+
+
 def test_batch_slice_with_absolute_offsets(hs_lib, torch):
     """A batch may be a slice of a larger packed array: offsets are absolute indices."""
     lens = [4096, 8192, 12, 65536, 20000]
