@@ -1059,6 +1059,7 @@ static void warm_t() {
     if constexpr (V == HS_STD) {
         occupancy<V, T, P2>();
         pair_occupancy<T, P2>();
+        if constexpr (sizeof(T) == 2) pair_occupancy<float, P2, true>();  // 16-bit batches via FP32 groups
     } else {
         zoned_occupancy<V, T, P2>();
     }
