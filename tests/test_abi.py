@@ -77,6 +77,26 @@ def test_plan_accepts_and_sizes_workspace(hs_lib):
     hs_lib.hs_plan_destroy(p)
 
 
+def test_16bit_eq1_plans_reserve_the_fp32_staging_region(hs_lib):
+    """Batched Eq. 1 over FP16/BF16 widens up to 64 spectra at a time into FP32 in the workspace, after
+    the control words and prefix sums, so such plans ask for min(n_spectra, 64) * max_bins * 4 bytes
+    there (the candidate sort, which runs after the sums, reuses the same space); other plans do not."""
+    mb = 1 << 16
+    sizes = {}
+    for name, dtype, variants in (("f32", hs_lib.F32, hs_lib.STD), ("f16", hs_lib.F16, hs_lib.STD),
+                                  ("bf16", hs_lib.BF16, hs_lib.STD), ("f16max", hs_lib.F16, hs_lib.MAX)):
+        p, _ = hs_lib.hs_plan_create(variants=variants, dtype=dtype, max_bins=mb)
+        sizes[name] = {n: hs_lib.hs_plan_workspace_size(p, n) for n in (1, 10, 64, 300)}
+        hs_lib.hs_plan_destroy(p)
+    for n in (1, 10, 64, 300):
+        stage = min(n, 64) * mb * 4
+        head = 256 + 8 * (n + 2)  # control words and tile prefix sums
+        for name in ("f16", "bf16"):
+            assert sizes[name][n] >= head + stage and sizes[name][n] >= sizes["f32"][n]
+            assert sizes[name][n] <= max(sizes["f32"][n], head + stage + 512)
+        assert sizes["f16max"][n] == sizes["f32"][n]
+
+
 def test_calls_validate_before_device_work(hs_lib):
     lib = hs_lib._lib
     p, _ = hs_lib.hs_plan_create(variants=hs_lib.FBIN)
